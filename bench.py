@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: DAMAS on the wavelet-compressed grid vs the full grid, one GB300.
+
+Workload: one frequency bin of the 81x81 scan (S = 6561) seen by a 64-microphone
+4-arm log spiral (1 m aperture) at 2 m, f = 2 kHz, three incoherent sources;
+Haar wavelet with 2 levels keeping 10% of the points (S~ = 657); 1000
+Gauss-Seidel sweeps; A stored in FP32.  Synthetic, seeded inputs.
+
+A step = one bin through the whole path on the compressed grid: DAS map,
+compressed grid (Algorithm 1), PSF matrix of the kept points, restriction of b,
+1000 sweeps, power map.  `value` is bins/s of that path with inputs resident in
+HBM; the full-grid path (DAS map, PSF matrix of all 6561 points, 1000 sweeps,
+power map) is timed beside it.  `e2e` repeats the compressed step through the
+same C-ABI calls with the CSM copied in from pinned host memory and the power map
+copied back every step.
+
+--impl reference times the oracle (plain FP64 CPU code) on the same workload.
+Multi-GPU (torchrun): every rank processes its own bins (bins are independent),
+no collective on the data path; value = all ranks' bins / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "DAMAS sweep HBM GB/s; freq-bins/s compressed vs full grid at 1e-4 rel err"
+UNIT = "freq-bins/s"
+ITERS = 1000
+LEVELS = 2
+KEEP = 0.10
+WORKLOAD = ("81x81 grid (S=6561) over 2x2 m at 2 m, M=64 4-arm log spiral (1 m), f=2 kHz, 3 incoherent "
+            "off-grid sources; Haar wavelet L=2 keeping 10% (S~=657); 1000 Gauss-Seidel sweeps; FP32 A")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1608_05179_gb300 import damas as D
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    sc = synth.scene_spiral_81(seed=1 + rank)
+    ctx = D.Context(local_rank)
+    geom = D.Geometry.from_scene(sc.mics, sc.grid, sc.c, device=dev)
+    C_dev = D.csm_tensor(sc.C, device=dev)
+    stream = torch.cuda.current_stream()
+    S = sc.grid.S
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    launches_per_step = 8  # steer+das, wavelet, gather, steer+psf, sweep, scatter
+
+    def compressed_step(C, sweep_ev=None):
+        b = D.das_map(ctx, geom, sc.freq, C)
+        idx, n_t, _, _ = D.wavelet_compress_grid(ctx, b, sc.grid.nx, sc.grid.ny, LEVELS, D.PRED_HAAR,
+                                                 D.EPS_KEEP_FRAC, KEEP)
+        n = int(n_t.item())
+        idx = idx[:n]
+        b_sub = D.damas_gather(ctx, b, idx, n)
+        A, g2 = D.damas_build_psf(ctx, geom, sc.freq, idx, n)
+        x = torch.empty(n, dtype=torch.float32, device=dev)
+        if sweep_ev:
+            sweep_ev[0].record(stream)
+        D.damas_solve(ctx, D.System(A, b_sub, x, ITERS), status=status)
+        if sweep_ev:
+            sweep_ev[1].record(stream)
+        xf, tot = D.damas_scatter_power(ctx, x, idx, g2, n, S)
+        return n, xf, tot
+
+    def full_step(C, sweep_ev=None):
+        b = D.das_map(ctx, geom, sc.freq, C)
+        A, g2 = D.damas_build_psf(ctx, geom, sc.freq, None, S, A=A_full, gnorm2=g2_full)
+        x = torch.empty(S, dtype=torch.float32, device=dev)
+        if sweep_ev:
+            sweep_ev[0].record(stream)
+        D.damas_solve(ctx, D.System(A, b, x, ITERS), status=status)
+        if sweep_ev:
+            sweep_ev[1].record(stream)
+        return D.damas_scatter_power(ctx, x, None, g2, S, S)
+
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    A_full = torch.empty((S, D.damas_lda(S)), dtype=torch.float32, device=dev)
+    g2_full = torch.empty(S, dtype=torch.float32, device=dev)
+
+    def timed(fn, K, W, *a):
+        for _ in range(W):
+            fn(*a)
+        torch.cuda.synchronize()
+        step_ms, sweep_ms, n_last = [], [], None
+        for _ in range(K):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            r = fn(*a, (ev[2], ev[3]))
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[1]))
+            sweep_ms.append(ev[2].elapsed_time(ev[3]))
+            n_last = r
+        if status.item() != 0:
+            raise RuntimeError(f"solver status {status.item()}")
+        return step_ms, sweep_ms, n_last
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    c_ms, c_sweep_ms, c_res = timed(compressed_step, args.steps, args.warmup, C_dev)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    k_full = max(2, args.steps // 2)
+    f_ms, f_sweep_ms, _ = timed(full_step, k_full, min(args.warmup, 3), C_dev)
+    clock_info = clocks.stop()
+    S_sub = int(c_res[0])
+
+    # e2e: CSM in from pinned host memory, power map out to pinned host memory, every step
+    C_host = C_dev.cpu().pin_memory()
+    mic_host = geom.mic_xyz.cpu().pin_memory()
+    x_host = torch.empty(S, dtype=torch.float32).pin_memory()
+    tot_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    C_e2e = torch.empty_like(C_dev)
+
+    def e2e_step(_ev=None):
+        C_e2e.copy_(C_host, non_blocking=True)
+        geom.mic_xyz.copy_(mic_host, non_blocking=True)
+        n, xf, tot = compressed_step(C_e2e)
+        x_host.copy_(xf, non_blocking=True)
+        tot_host.copy_(tot, non_blocking=True)
+        return n
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    h2d = C_host.numel() * C_host.element_size() + mic_host.numel() * mic_host.element_size()
+    d2h = x_host.numel() * 4 + 8
+
+    # max over ranks
+    tot_c = float(sum(c_ms))
+    tot_f = float(sum(f_ms))
+    tot_e = float(sum(e_ms))
+    if world > 1:
+        t = torch.tensor([tot_c, tot_f, tot_e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_c, tot_f, tot_e = t.tolist()
+    ms_step = tot_c / args.steps
+    value = world * args.steps / (tot_c / 1e3)
+    full_bins = world * k_full / (tot_f / 1e3)
+    e2e_val = world * args.steps / (tot_e / 1e3)
+
+    hbm_peak, peak_kind = _peaks()
+    lda_c = D.damas_lda(S_sub)
+    bytes_c = float(S_sub) * S_sub * 4 * ITERS                  # A read once per sweep
+    sweep_c_ms = statistics.mean(c_sweep_ms)
+    ach_c = bytes_c / (sweep_c_ms / 1e3) / 1e9
+    bytes_f = float(S) * S * 4 * ITERS
+    sweep_f_ms = statistics.mean(f_sweep_ms)
+    ach_f = bytes_f / (sweep_f_ms / 1e3) / 1e9
+    traffic = _traffic_from_profiles()
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene; no dataset)",
+        "config": {"workload": WORKLOAD, "S": S, "S_compressed": S_sub, "M": sc.M, "iters": ITERS,
+                   "a_dtype": "f32", "l2": "flushed between steps (512 MB write outside the timed events)",
+                   "parallelism": f"bin-sharded x{world}" if world > 1 else "single GPU"},
+        "full_grid": {"value": round(full_bins, 3), "unit": UNIT, "ms_per_bin": round(tot_f / k_full, 3),
+                      "steps": k_full, "sweep_ms": round(sweep_f_ms, 3), "sweep_gbs": round(ach_f, 1),
+                      "speedup_compressed_vs_full": round(value / full_bins, 2)},
+        "roofline": {"kernel": "damas_sweep_kernel (compressed grid)", "bound": "hbm", "achieved": round(ach_c, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_c / hbm_peak, 4),
+                     "traffic": traffic.get("compressed"), "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_c, "launch_ms": round(sweep_c_ms, 4),
+                     "note": "A (S~ x S~ FP32, 1.7 MB) is read once per sweep in the algorithm; the kernel keeps it "
+                             "in shared memory, so the launch is bound by the sequential row chain, not HBM"},
+        "roofline_full_grid": {"kernel": "damas_sweep_kernel (full grid)", "bound": "hbm", "achieved": round(ach_f, 1),
+                               "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_f / hbm_peak, 4),
+                               "traffic": traffic.get("full"), "algorithmic_bytes_per_launch": bytes_f,
+                               "launch_ms": round(sweep_f_ms, 3)},
+        "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clock_info,
+        "wall_s_compressed_region": round(wall, 3),
+    }
+    ctx.close()
+    return out
+
+
+def _traffic_from_profiles():
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except ValueError:
+            return {}
+    return {}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def oracle_bins(seconds: float, min_bins: int = 2, max_bins: int = 1000):
+    import oracle as O
+    sc = synth.scene_spiral_81(seed=1)
+    n, t0 = 0, time.perf_counter()
+    while n < min_bins or (time.perf_counter() - t0 < seconds and n < max_bins):
+        O.solve_bin(sc.mics, sc.grid, sc.freq, sc.c, sc.C, ITERS, compressed=True, levels=LEVELS,
+                    predictor=O.PRED_HAAR, eps_mode=O.EPS_KEEP_FRAC, eps=KEEP)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n, dt
+
+
+def cpu_baseline(seconds=12.0):
+    n, dt = oracle_bins(seconds)
+    return {"value": round(n / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} bins of the same workload through the oracle's compressed path "
+                      f"(DAS map, Algorithm 1, PSF matrix, 1000 FP64 sweeps), single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    import oracle as O  # noqa: F401
+    for _ in range(args.warmup):
+        oracle_bins(0.0, min_bins=1, max_bins=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_bins(0.0, min_bins=1, max_bins=1)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    return {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene; no dataset)",
+            "config": {"workload": WORKLOAD}, "impl": "reference",
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed bins (one per step) after {args.warmup} warm-up bins"},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    from paper_1608_05179_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * damas.h - C ABI of the GB300 DAMAS library (libdamas.so).
+ *
+ * Hot path of Ma & Liu, "Improving the Efficiency of DAMAS for Sound Source
+ * Localization via Wavelet Compression Computational Grid": steering vectors,
+ * PSF matrix, DAS map, wavelet-compressed grid, and the DAMAS Gauss-Seidel
+ * iteration, on the full scan grid or on the compressed one.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: DAMAS_OK (0) or a negative code.
+ *    damas_last_error() returns a message for the last failure on a context.
+ *  - Buffers are owned by the caller.  Pointers named *_dev are device pointers
+ *    on the context's device; every call enqueues its work on the given stream
+ *    and returns without waiting, unless its comment says otherwise.  Device
+ *    results are valid once the stream has reached the call.
+ *  - Arguments are validated on the host before anything is enqueued; a bad
+ *    argument returns DAMAS_EINVAL and enqueues nothing.
+ *  - A context owns scratch device memory (grown on demand, outside any
+ *    captured region) that calls on that context share: issue the calls of one
+ *    context on one stream, or serialise them.
+ *  - Scan grid (§2): nx x ny points at (x0 + ix*dx, y0 + iy*dy, z), index
+ *    n = iy*nx + ix; the array centre is the origin.
+ *  - Equation numbers follow the order of the paper's displayed equations:
+ *    (2) DAS map, (4) steering v, (7) propagation g, (10) PSF, (12) Ax=b,
+ *    (13)-(14) Gauss-Seidel with clamp, (15) nested grids, (22) compressed
+ *    grid, (23) wavelet coefficient, (24) compressed system; Algorithm 1.
+ */
+#ifndef DAMAS_H
+#define DAMAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct damas_ctx damas_ctx;
+/* A CUDA stream handle (cudaStream_t); NULL selects the legacy default stream. */
+typedef void *damas_stream;
+
+enum {
+    DAMAS_OK = 0,
+    DAMAS_EINVAL = -1,    /* invalid argument (nothing was enqueued) */
+    DAMAS_ENOMEM = -2,    /* scratch allocation failed */
+    DAMAS_ECUDA = -3,     /* a CUDA runtime call failed */
+    DAMAS_ETIMEDOUT = -4, /* a bounded device-side wait gave up (see damas_solve) */
+    DAMAS_EBUSY = -5,     /* resource busy (serving queue full) */
+    DAMAS_ENOTFOUND = -6  /* unknown ticket */
+};
+
+/* PSF-matrix formulations.
+ * E: e_n = g_n / ||g_n|| with g of Eq. (7); A_nm = |e_n^H e_m|^2, b_n = Re(e_n^H C e_n).
+ *    A is symmetric, positive semi-definite, with unit diagonal.  The solution is
+ *    x'_n = x_n ||g_n||^2; damas_scatter_power divides by ||g_n||^2.
+ * P: the paper's literal v (Eq. (4)) and g (Eq. (7)): A_ns = PSF(r_n|r_s) =
+ *    |v_n^H g_s|^2 / M^2 (Eq. (10)), b_n = Re(v_n^H C v_n) / M^2 (Eq. (2));
+ *    unit diagonal, not symmetric; x is in power units directly. */
+enum { DAMAS_FORM_E = 0, DAMAS_FORM_P = 1 };
+
+/* Storage type of A. */
+enum { DAMAS_F32 = 1, DAMAS_BF16 = 2 };
+
+/* Interpolation used by the wavelet coefficient of Eq. (23):
+ * LINEAR (edge: mean of the two coarse neighbours, centre: mean of the four
+ * coarse corners) or HAAR (constant: the lower-left coarse neighbour). */
+enum { DAMAS_PRED_LINEAR = 0, DAMAS_PRED_HAAR = 1 };
+
+/* How the threshold eps of Eq. (22) is formed:
+ * ABS       eps as given;
+ * REL_MAX   eps * max_n b_n (FP32 product);
+ * KEEP_FRAC eps is a fraction f: the threshold is the K-th largest |detail|
+ *           outside G^0 with K = ceil(f * nx * ny) - |G^0| (K <= 0 keeps G^0
+ *           only; ties at the threshold are all kept). */
+enum { DAMAS_EPS_ABS = 0, DAMAS_EPS_REL_MAX = 1, DAMAS_EPS_KEEP_FRAC = 2 };
+
+typedef struct {
+    int M;                   /* number of microphones, 1..DAMAS_MAX_MICS */
+    const double *mic_xyz_dev; /* device, M x 3 doubles (x, y, z) in metres, array plane z = 0 */
+    int nx, ny;              /* scan grid size, S = nx * ny */
+    double x0, y0, dx, dy, z; /* scan grid origin, spacing and plane distance (metres) */
+    double c;                /* speed of sound c0 (m/s); k = 2 pi f / c0 (§2) */
+    int formulation;         /* DAMAS_FORM_E or DAMAS_FORM_P */
+} damas_geom;
+
+#define DAMAS_MAX_MICS 256
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  Allocates nothing yet. */
+int damas_create(damas_ctx **out, int device);
+/* Free the context and its scratch memory (synchronises the device). */
+int damas_destroy(damas_ctx *ctx);
+/* Message of the last failed call on ctx (static storage owned by ctx). */
+const char *damas_last_error(const damas_ctx *ctx);
+/* Row stride, in elements, that the library uses for an S x S matrix A:
+ * S rounded up to a multiple of 32 (every row 128-byte aligned for FP32). */
+int damas_lda(int S);
+
+/* ------------------------------------------------------------------ a1 + a4: PSF matrix */
+
+/*
+ * PSF matrix of Eq. (10) arranged as A of Eq. (12), restricted to a set of grid
+ * points (Eq. (24)) when idx_dev is given.
+ *   idx_dev   device int32[S_sub], ascending grid indices, or NULL for all
+ *             S = nx*ny points in order (then S_sub must equal S).
+ *   A_dev     device, S_sub x lda, row-major, lda = damas_lda(S_sub); FP32 when
+ *             a_dtype = DAMAS_F32, bfloat16 when DAMAS_BF16.  A[n][m] for the
+ *             n-th and m-th selected points; the diagonal is stored as exactly 1;
+ *             padding columns S_sub..lda-1 are written as 0.
+ *   gnorm2_dev optional device float[S_sub]: ||g_n||^2 of the selected points
+ *             (formulation E uses it to turn x' into power).
+ * Steering and propagation vectors are formed with the phase k*d in FP64,
+ * reduced to a fraction of a period before an FP32 sine/cosine; the complex
+ * Gram products accumulate in FP32.
+ */
+int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev,
+                    int S_sub, int a_dtype, void *A_dev, int lda, float *gnorm2_dev, damas_stream stream);
+
+/* ------------------------------------------------------------------ a2: DAS map */
+
+/*
+ * Mean-square DAS map of Eq. (2) on the full grid.
+ *   C_dev  device, M x M complex cross-spectral matrix (Eq. (1)), row-major,
+ *          interleaved (re, im) FP32 pairs; assumed Hermitian.
+ *   b_dev  device float[nx*ny] output, FP32, real part of v^H C v (scaled as
+ *          the formulation says).
+ */
+int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float *C_dev, float *b_dev,
+            damas_stream stream);
+
+/* ------------------------------------------------------------------ a3: compressed grid */
+
+typedef struct {
+    int levels;     /* J of Algorithm 1: level-0 grid = multiples of 2^J on both axes; 1..15 */
+    int predictor;  /* DAMAS_PRED_LINEAR or DAMAS_PRED_HAAR */
+    int eps_mode;   /* DAMAS_EPS_ABS, DAMAS_EPS_REL_MAX or DAMAS_EPS_KEEP_FRAC */
+    double eps;     /* threshold, or kept fraction for KEEP_FRAC */
+} damas_wavelet_cfg;
+
+/*
+ * Algorithm 1: the wavelet-compressed computational grid of the map b.
+ * For j = J-1 down to 0 every point of G^{j+1} \ G^j is kept when
+ * |interpolated(b from G^j) - b| >= eps (Eq. (22)-(23)); G^0 is always kept;
+ * the result is the union as ascending grid indices.  The interpolation, the
+ * threshold and the comparison are evaluated in FP32 in a fixed order:
+ * edge = 0.5f*(a + c), centre = 0.25f*((b(-,-) + b(+,-)) + (b(-,+) + b(+,+))),
+ * detail = prediction - b.  Coarse neighbours beyond the last row or column do
+ * not exist; the prediction then averages the neighbours that do.
+ *   b_dev       device float[nx*ny] input map.
+ *   idx_dev     device int32[nx*ny] (capacity) output, ascending.
+ *   S_sub_dev   device int32[1] output: the number of kept points S~.
+ *   detail_dev  optional device float[nx*ny]: prediction - b (0 on G^0).
+ *   eps_abs_dev optional device float[1]: the absolute threshold used.
+ * Limits: nx, ny in 1..65535, nx*ny <= 4194304.
+ */
+int wavelet_compress_grid(damas_ctx *ctx, const float *b_dev, int nx, int ny, const damas_wavelet_cfg *cfg,
+                          int32_t *idx_dev, int32_t *S_sub_dev, float *detail_dev, float *eps_abs_dev,
+                          damas_stream stream);
+
+/* ------------------------------------------------------------------ a5, a7: restriction and scatter */
+
+/* dst[i] = src[idx[i]], i < n (b~ of Eq. (24)). */
+int damas_gather(damas_ctx *ctx, const float *src_dev, const int32_t *idx_dev, int n, float *dst_dev,
+                 damas_stream stream);
+
+/*
+ * Compressed-grid solution back onto the full grid (§5: zero off the kept
+ * points), converted to power units:
+ *   x_full[idx[i]] = x_sub[i] / gnorm2[i]   (gnorm2_dev given, formulation E)
+ *   x_full[idx[i]] = x_sub[i]               (gnorm2_dev NULL)
+ * every other entry of x_full[S] is set to 0.  idx_dev NULL means the identity
+ * (n == S).  total_power_dev (optional, device double[1]) receives the
+ * integrated power sum_n x_full[n] (Table 1), summed in FP64 in a fixed order.
+ */
+int damas_scatter_power(damas_ctx *ctx, const float *x_sub_dev, const int32_t *idx_dev, const float *gnorm2_dev,
+                        int n, float *x_full_dev, int S, double *total_power_dev, damas_stream stream);
+
+/* ------------------------------------------------------------------ a6: DAMAS iteration */
+
+/* How a solve starts. */
+enum {
+    DAMAS_INIT_ZERO = 0,  /* x^0 = 0 (the paper's choice, §3); x_dev is overwritten */
+    DAMAS_INIT_X = 1,     /* continue from x_dev: the residual A x - b is recomputed */
+    DAMAS_INIT_STATE = 2  /* continue from x_dev and the residual kept in state_dev by
+                             an earlier solve of the same system: bit-identical to one
+                             longer solve */
+};
+
+typedef struct {
+    const void *A_dev;  /* S x lda, row-major, FP32 or BF16 (a_dtype), unit diagonal */
+    int a_dtype;        /* DAMAS_F32 or DAMAS_BF16 */
+    int lda;            /* row stride in elements, multiple of 8, >= S */
+    int S;              /* number of unknowns, >= 1 */
+    const float *b_dev; /* device float[S] */
+    float *x_dev;       /* device float[S], in/out */
+    float *state_dev;   /* optional device float[2*S]: the residual as an unevaluated
+                           FP32 pair (hi, lo); written at the end of every solve,
+                           read with DAMAS_INIT_STATE */
+    int init;           /* DAMAS_INIT_* */
+    int iters;          /* number of sweeps T >= 0 */
+} damas_system;
+
+typedef struct {
+    int ctas_per_system;  /* 0 = automatic; otherwise the number of cooperating CTAs per system */
+    int timeout_ms;       /* bound on every device-side wait, default (0) 2000 ms */
+    int32_t *status_dev;  /* optional device int32[1]: receives DAMAS_OK or DAMAS_ETIMEDOUT;
+                             when given the call does not synchronise */
+    int withhold_block;   /* test hook for the bounded waits, 0 in normal use: when > 0 the
+                             owner of row block (withhold_block - 1) never publishes it, so
+                             the waits of the other CTAs for it run out */
+} damas_solve_cfg;
+
+/*
+ * DAMAS iteration, Eq. (13)-(14) (§3), for nsys independent systems in one
+ * persistent launch: for each sweep, for i = 1..S in order,
+ *   r_i = sum_{j<i} A_ij x_j^(n+1) + sum_{j>=i} A_ij x_j^(n) - b_i,
+ *   x_i = max(x_i - r_i / A_ii, 0),  with A_ii = 1.
+ * The row order is exactly the paper's.  Rows are processed in blocks of 32:
+ * a block is solved sequentially on chip from its residual, then the change of
+ * x is applied to the residual of every other row (A[:,J] dx_J).  The residual
+ * is carried as an FP32 (hi, lo) pair updated with error-free transformations,
+ * so it does not drift over thousands of sweeps.
+ *   sys    host array of nsys descriptors (copied before the call returns).
+ *   cfg    optional (NULL = defaults).
+ * Each system is solved by a team of CTAs that run concurrently (a cooperative
+ * launch; every team must fit on the device at once).  Every device-side wait
+ * is bounded by cfg->timeout_ms; a wait that runs out makes the kernel stop and
+ * report DAMAS_ETIMEDOUT.  Without cfg->status_dev the call synchronises the
+ * stream and returns that status; with it the call returns at once and the
+ * status lands in *status_dev.
+ */
+int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg,
+                damas_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DAMAS_H */

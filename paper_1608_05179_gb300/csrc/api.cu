@@ -1,0 +1,418 @@
+// C ABI of libdamas.so: argument checks, scratch management and launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "sweep.cuh"
+
+// ----------------------------------------------------------------------------- context helpers
+int ctx_fail(damas_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int ctx_ensure(damas_ctx *ctx, ScratchBuf &b, size_t bytes) {
+    if (bytes <= b.cap) return DAMAS_OK;
+    if (b.ptr) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "sync before scratch growth: %s", cudaGetErrorString(e));
+        cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.cap = 0;
+    }
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    cap = (cap + 4095) / 4096 * 4096;
+    if (cudaMalloc(&b.ptr, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, DAMAS_ENOMEM, "scratch allocation of %zu bytes failed", cap);
+    }
+    b.cap = cap;
+    return DAMAS_OK;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int check_geom(damas_ctx *ctx, const damas_geom *g) {
+    if (!g) return ctx_fail(ctx, DAMAS_EINVAL, "geom is NULL");
+    if (g->M < 1 || g->M > DAMAS_MAX_MICS) return ctx_fail(ctx, DAMAS_EINVAL, "M=%d out of range", g->M);
+    if (!g->mic_xyz_dev) return ctx_fail(ctx, DAMAS_EINVAL, "mic_xyz_dev is NULL");
+    if (g->nx < 1 || g->ny < 1 || (long long)g->nx * g->ny > (1ll << 26))
+        return ctx_fail(ctx, DAMAS_EINVAL, "grid %dx%d out of range", g->nx, g->ny);
+    if (!(g->c > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "speed of sound must be positive");
+    if (g->formulation != DAMAS_FORM_E && g->formulation != DAMAS_FORM_P)
+        return ctx_fail(ctx, DAMAS_EINVAL, "unknown formulation %d", g->formulation);
+    return DAMAS_OK;
+}
+
+GeomK to_kernel(const damas_geom *g, double f) {
+    GeomK k;
+    k.mic = g->mic_xyz_dev;
+    k.M = g->M;
+    k.nx = g->nx;
+    k.ny = g->ny;
+    k.x0 = g->x0;
+    k.y0 = g->y0;
+    k.dx = g->dx;
+    k.dy = g->dy;
+    k.z = g->z;
+    k.f_over_c = f / g->c;
+    k.form = g->formulation;
+    return k;
+}
+
+inline int planes_ld(int M) { return round_up(M, 4); }
+
+}  // namespace
+
+extern "C" {
+
+int damas_create(damas_ctx **out, int device) {
+    if (!out) return DAMAS_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return DAMAS_EINVAL;
+    }
+    damas_ctx *ctx = new damas_ctx();
+    ctx->device = device;
+    DeviceGuard dg(device);
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    ctx->sm_count = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    ctx->smem_optin = (size_t)v;
+    *out = ctx;
+    return DAMAS_OK;
+}
+
+int damas_destroy(damas_ctx *ctx) {
+    if (!ctx) return DAMAS_EINVAL;
+    {
+        DeviceGuard dg(ctx->device);
+        cudaDeviceSynchronize();
+        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc})
+            if (b->ptr) cudaFree(b->ptr);
+    }
+    delete ctx;
+    return DAMAS_OK;
+}
+
+const char *damas_last_error(const damas_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int damas_lda(int S) { return S <= 0 ? 0 : round_up(S, 32); }
+
+// ----------------------------------------------------------------------------- PSF matrix
+int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev, int S_sub,
+                    int a_dtype, void *A_dev, int lda, float *gnorm2_dev, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    int rc = check_geom(ctx, geom);
+    if (rc) return rc;
+    const long long S = (long long)geom->nx * geom->ny;
+    if (!(freq_hz > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "frequency must be positive");
+    if (S_sub < 1 || S_sub > S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub=%d out of range", S_sub);
+    if (!idx_dev && S_sub != S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub must equal nx*ny when idx is NULL");
+    if (a_dtype != DAMAS_F32 && a_dtype != DAMAS_BF16) return ctx_fail(ctx, DAMAS_EINVAL, "bad a_dtype");
+    if (!A_dev) return ctx_fail(ctx, DAMAS_EINVAL, "A_dev is NULL");
+    if (lda < S_sub || lda % 32) return ctx_fail(ctx, DAMAS_EINVAL, "lda=%d must be a multiple of 32 and >= S_sub", lda);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ldm = planes_ld(geom->M);
+    const int nplanes = geom->formulation == DAMAS_FORM_P ? 4 : 2;
+    const size_t plane = (size_t)S_sub * ldm;
+    rc = ctx_ensure(ctx, ctx->planes, plane * nplanes * sizeof(float));
+    if (rc) return rc;
+    float *base = (float *)ctx->planes.ptr;
+    float *Lre = base, *Lim = base + plane;
+    float *Rre = nplanes == 4 ? base + 2 * plane : Lre, *Rim = nplanes == 4 ? base + 3 * plane : Lim;
+    GeomK gk = to_kernel(geom, freq_hz);
+    const int kind = geom->formulation == DAMAS_FORM_P ? 2 : 0;
+    DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, idx_dev, S_sub, Lre, Lim, Rre, Rim, ldm, gnorm2_dev, st));
+    const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
+    DAMAS_CUDA_TRY(ctx, launch_psf_gram(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, a_dtype, st));
+    return DAMAS_OK;
+}
+
+// ----------------------------------------------------------------------------- DAS map
+int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float *C_dev, float *b_dev,
+            damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    int rc = check_geom(ctx, geom);
+    if (rc) return rc;
+    if (!(freq_hz > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "frequency must be positive");
+    if (!C_dev || !b_dev) return ctx_fail(ctx, DAMAS_EINVAL, "C_dev and b_dev are required");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = geom->nx * geom->ny;
+    const int ldm = planes_ld(geom->M);
+    const size_t plane = (size_t)S * ldm;
+    rc = ctx_ensure(ctx, ctx->planes, plane * 2 * sizeof(float));
+    if (rc) return rc;
+    float *Lre = (float *)ctx->planes.ptr, *Lim = Lre + plane;
+    GeomK gk = to_kernel(geom, freq_hz);
+    // the vector the map is steered with: e (E) or v (P)
+    const int kind = geom->formulation == DAMAS_FORM_P ? 1 : 0;
+    DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, nullptr, S, Lre, Lim, nullptr, nullptr, ldm, nullptr, st));
+    const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
+    DAMAS_CUDA_TRY(ctx, launch_das(Lre, Lim, ldm, geom->M, S, C_dev, scale, b_dev, st));
+    return DAMAS_OK;
+}
+
+// ----------------------------------------------------------------------------- compressed grid
+int wavelet_compress_grid(damas_ctx *ctx, const float *b_dev, int nx, int ny, const damas_wavelet_cfg *cfg,
+                          int32_t *idx_dev, int32_t *S_sub_dev, float *detail_dev, float *eps_abs_dev,
+                          damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (!cfg) return ctx_fail(ctx, DAMAS_EINVAL, "cfg is NULL");
+    if (!b_dev || !idx_dev || !S_sub_dev) return ctx_fail(ctx, DAMAS_EINVAL, "b_dev, idx_dev, S_sub_dev are required");
+    if (nx < 1 || ny < 1 || nx > 65535 || ny > 65535 || (long long)nx * ny > 4194304)
+        return ctx_fail(ctx, DAMAS_EINVAL, "grid %dx%d out of range", nx, ny);
+    if (cfg->levels < 1 || cfg->levels > 15) return ctx_fail(ctx, DAMAS_EINVAL, "levels=%d out of range", cfg->levels);
+    if (cfg->predictor != DAMAS_PRED_LINEAR && cfg->predictor != DAMAS_PRED_HAAR)
+        return ctx_fail(ctx, DAMAS_EINVAL, "unknown predictor");
+    if (cfg->eps_mode < DAMAS_EPS_ABS || cfg->eps_mode > DAMAS_EPS_KEEP_FRAC)
+        return ctx_fail(ctx, DAMAS_EINVAL, "unknown eps_mode");
+    if (!(cfg->eps >= 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "eps must be >= 0");
+    if (cfg->eps_mode == DAMAS_EPS_KEEP_FRAC && cfg->eps > 1.0)
+        return ctx_fail(ctx, DAMAS_EINVAL, "keep fraction must be in [0, 1]");
+    DeviceGuard dg(ctx->device);
+    const int S = nx * ny;
+    int rc = ctx_ensure(ctx, ctx->wave, (size_t)S * sizeof(float));
+    if (rc) return rc;
+    const int J = cfg->levels;
+    const long long n0 = (long long)(((nx - 1) >> J) + 1) * (((ny - 1) >> J) + 1);
+    const long long K = cfg->eps_mode == DAMAS_EPS_KEEP_FRAC ? (long long)ceil(cfg->eps * (double)S) - n0 : 0;
+    DAMAS_CUDA_TRY(ctx, launch_wavelet(b_dev, nx, ny, J, cfg->predictor, cfg->eps_mode, (float)cfg->eps, (float)cfg->eps,
+                                       K, idx_dev, S_sub_dev, detail_dev, eps_abs_dev, (float *)ctx->wave.ptr,
+                                       (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
+// ----------------------------------------------------------------------------- gather / scatter
+int damas_gather(damas_ctx *ctx, const float *src_dev, const int32_t *idx_dev, int n, float *dst_dev,
+                 damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (n < 0 || (n > 0 && (!src_dev || !idx_dev || !dst_dev))) return ctx_fail(ctx, DAMAS_EINVAL, "bad gather arguments");
+    DeviceGuard dg(ctx->device);
+    DAMAS_CUDA_TRY(ctx, launch_gather(src_dev, idx_dev, n, dst_dev, (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
+int damas_scatter_power(damas_ctx *ctx, const float *x_sub_dev, const int32_t *idx_dev, const float *gnorm2_dev,
+                        int n, float *x_full_dev, int S, double *total_power_dev, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (S < 1 || n < 0 || n > S || !x_full_dev || (n > 0 && !x_sub_dev))
+        return ctx_fail(ctx, DAMAS_EINVAL, "bad scatter arguments");
+    if (!idx_dev && n != S) return ctx_fail(ctx, DAMAS_EINVAL, "n must equal S when idx is NULL");
+    DeviceGuard dg(ctx->device);
+    DAMAS_CUDA_TRY(ctx, launch_scatter_power(x_sub_dev, idx_dev, gnorm2_dev, n, x_full_dev, S, total_power_dev,
+                                             (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
+// ----------------------------------------------------------------------------- DAMAS iteration
+namespace {
+
+struct Plan {
+    int ncta, R, resident;
+    size_t smem;
+};
+
+Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int cta_budget) {
+    const int nb = (s.S + 31) / 32;
+    const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
+    Plan p{};
+    auto finish = [&](int R, bool res) {
+        p.R = R;
+        p.ncta = (nb * 32 + R - 1) / R;
+        p.resident = res ? 1 : 0;
+        p.smem = sweep_smem_bytes(R, s.lda, s.a_dtype, res);
+    };
+    if (forced > 0) {
+        const int P = std::min(forced, nb);
+        const int R = (nb + P - 1) / P * 32;
+        finish(R, sweep_smem_bytes(R, s.lda, s.a_dtype, true) <= budget);
+        return p;
+    }
+    // rows of A that fit in shared memory next to x and the residual
+    const size_t per_row = sweep_smem_bytes(1, s.lda, s.a_dtype, true);
+    const int rmax = (int)std::min<size_t>(budget / per_row, (size_t)1 << 20) / 32 * 32;
+    if (rmax >= 32) {
+        const int P = (nb * 32 + rmax - 1) / rmax;
+        if (P <= cta_budget) {
+            const int R = (nb + P - 1) / P * 32;
+            finish(R, true);
+            return p;
+        }
+    }
+    const int P = std::max(1, std::min(nb, cta_budget));
+    finish((nb + P - 1) / P * 32, false);
+    return p;
+}
+
+}  // namespace
+
+int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (nsys < 0 || (nsys > 0 && !sys)) return ctx_fail(ctx, DAMAS_EINVAL, "bad system array");
+    if (nsys == 0) return DAMAS_OK;
+    for (int i = 0; i < nsys; ++i) {
+        const damas_system &s = sys[i];
+        if (s.S < 1) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: S=%d", i, s.S);
+        if (!s.A_dev || !s.b_dev || !s.x_dev) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: NULL pointer", i);
+        if (s.a_dtype != DAMAS_F32 && s.a_dtype != DAMAS_BF16) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: a_dtype", i);
+        if (s.lda < round_up(s.S, 32) || s.lda % 32)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: lda=%d must be a multiple of 32 and >= S rounded up to 32", i,
+                            s.lda);
+        if (s.init < DAMAS_INIT_ZERO || s.init > DAMAS_INIT_STATE) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: init", i);
+        if (s.init == DAMAS_INIT_STATE && !s.state_dev)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: INIT_STATE needs state_dev", i);
+        if (s.iters < 0 || s.iters > (1 << 24)) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: iters=%d", i, s.iters);
+    }
+    const int forced = cfg ? cfg->ctas_per_system : 0;
+    const long long timeout_ms = (cfg && cfg->timeout_ms > 0) ? cfg->timeout_ms : 2000;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // plan every system, then pack them into launches that fit on the device at once
+    std::vector<Plan> plans(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        plans[i] = plan_system(ctx, sys[i], forced, ctx->sm_count);
+        int occ = 0;
+        cudaError_t e = sweep_occupancy(plans[i].smem, &occ);
+        if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+        if (plans[i].ncta > occ * ctx->sm_count)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d needs %d co-resident CTAs, the device holds %d", i,
+                            plans[i].ncta, occ * ctx->sm_count);
+    }
+    struct Launch {
+        std::vector<int> ids;
+        size_t smem = 0;
+        int ctas = 0;
+        int max_iters = 0;
+    };
+    std::vector<Launch> launches;
+    {
+        Launch cur;
+        for (int i = 0; i < nsys; ++i) {
+            const Plan &pl = plans[i];
+            const size_t smem = std::max(cur.smem, pl.smem);
+            int occ = 0;
+            cudaError_t e = sweep_occupancy(smem, &occ);
+            if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+            const int cap = occ * ctx->sm_count;
+            if (!cur.ids.empty() && ((int)cur.ids.size() == SWEEP_MAX_SYS || cur.ctas + pl.ncta > cap)) {
+                launches.push_back(cur);
+                cur = Launch();
+            }
+            cur.ids.push_back(i);
+            cur.smem = std::max(cur.smem, pl.smem);
+            cur.ctas += pl.ncta;
+            cur.max_iters = std::max(cur.max_iters, sys[i].iters);
+        }
+        if (!cur.ids.empty()) launches.push_back(cur);
+    }
+    // exchange buffers: a flag region (nb words per system) followed by the dx
+    // region (nb*32 floats per system), each sized for the largest launch.  Flag
+    // words only ever hold epoch-tagged flags, so stale ones always compare old.
+    size_t need_flags = 0, need_dx = 0;
+    for (const Launch &L : launches) {
+        size_t f = 0, d = 0;
+        for (int i : L.ids) {
+            const size_t nb = (size_t)(sys[i].S + 31) / 32;
+            f += (size_t)round_up((int)nb, 4) * sizeof(unsigned);
+            d += nb * 32 * sizeof(float);
+        }
+        need_flags = std::max(need_flags, f);
+        need_dx = std::max(need_dx, d);
+    }
+    const size_t flag_bytes = std::max(ctx->solve_flag_bytes, (need_flags + 65535) / 65536 * 65536);
+    const bool relayout = flag_bytes != ctx->solve_flag_bytes || flag_bytes + need_dx > ctx->solve.cap;
+    int rc = ctx_ensure(ctx, ctx->solve, flag_bytes + need_dx);
+    if (rc) return rc;
+    if (relayout) {
+        DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->solve.ptr, 0, ctx->solve.cap, st));
+        ctx->solve_flag_bytes = flag_bytes;
+        ctx->epoch = 0;
+    }
+    rc = ctx_ensure(ctx, ctx->status, 64);
+    if (rc) return rc;
+    int *status = cfg && cfg->status_dev ? cfg->status_dev : (int *)ctx->status.ptr;
+    DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+
+    for (const Launch &L : launches) {
+        if ((unsigned long long)ctx->epoch + L.max_iters + 2 >= (1ull << 30)) {
+            DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->solve.ptr, 0, ctx->solve.cap, st));
+            ctx->epoch = 0;
+        }
+        SweepParams p;
+        memset(&p, 0, sizeof(p));
+        p.nsys = (int)L.ids.size();
+        p.status = status;
+        p.active_blocks = nullptr;
+        p.timeout_ns = (unsigned long long)timeout_ms * 1000000ull;
+        p.withhold_block = (cfg && cfg->withhold_block > 0) ? cfg->withhold_block - 1 : -1;
+        char *fl = (char *)ctx->solve.ptr;
+        char *ex = fl + ctx->solve_flag_bytes;
+        int cta = 0;
+        for (int q = 0; q < p.nsys; ++q) {
+            const int i = L.ids[q];
+            const damas_system &s = sys[i];
+            const Plan &pl = plans[i];
+            const int nb = (s.S + 31) / 32;
+            SweepSys &d = p.sys[q];
+            d.A = s.A_dev;
+            d.b = s.b_dev;
+            d.x = s.x_dev;
+            d.state = s.state_dev;
+            d.dbuf = (float *)ex;
+            ex += (size_t)nb * 32 * sizeof(float);
+            d.flags = (unsigned *)fl;
+            fl += (size_t)round_up(nb, 4) * sizeof(unsigned);
+            d.lda = s.lda;
+            d.S = s.S;
+            d.dtype = s.a_dtype;
+            d.init = s.init;
+            d.iters = s.iters;
+            d.cta0 = cta;
+            d.ncta = pl.ncta;
+            d.rows_per_cta = pl.R;
+            d.resident = pl.resident;
+            d.epoch0 = ctx->epoch;
+            cta += pl.ncta;
+        }
+        DAMAS_CUDA_TRY(ctx, launch_sweep(p, cta, L.smem, st));
+        ctx->epoch += (unsigned)L.max_iters + 1u;
+    }
+    if (cfg && cfg->status_dev) return DAMAS_OK;
+    int h = 0;
+    DAMAS_CUDA_TRY(ctx, cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DAMAS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (h != 0) return ctx_fail(ctx, h, "solver wait timed out after %lld ms", timeout_ms);
+    return DAMAS_OK;
+}
+
+}  // extern "C"

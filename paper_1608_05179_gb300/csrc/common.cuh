@@ -1,0 +1,87 @@
+// Shared definitions of the DAMAS CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/damas.h"
+
+// ----------------------------------------------------------------------------- context
+struct ScratchBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+};
+
+struct damas_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;  // max dynamic shared memory per block (opt-in)
+    char err[512] = {0};
+    // scratch, grown on demand
+    ScratchBuf planes;   // steering / propagation vectors
+    ScratchBuf wave;     // wavelet work arrays
+    ScratchBuf solve;    // solver exchange buffers and flags
+    ScratchBuf status;   // solver status words
+    ScratchBuf misc;
+    unsigned int epoch = 0;      // flag epoch of the solver exchange buffers
+    size_t solve_flag_bytes = 0; // size of the flag region at the start of `solve`
+};
+
+int ctx_fail(damas_ctx *ctx, int code, const char *fmt, ...);
+int ctx_ensure(damas_ctx *ctx, ScratchBuf &b, size_t bytes);
+
+#define DAMAS_CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return ctx_fail((ctx), DAMAS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Geometry as the kernels see it.
+struct GeomK {
+    const double *mic;  // M x 3
+    int M;
+    int nx, ny;
+    double x0, y0, dx, dy, z;
+    double f_over_c;    // k / (2 pi): cycles per metre
+    int form;
+};
+
+// ----------------------------------------------------------------------------- kernel launchers
+// Vectors of n points (grid indices idx[i], or i when idx is NULL) as FP32
+// planes [n][ldm].  kind 0: L = e (formulation E); 1: L = v; 2: L = v, R = g
+// (formulation P).  gnorm2 (optional) receives ||g||^2.
+cudaError_t launch_steer(const GeomK &g, int kind, const int32_t *idx, int n, float *Lre, float *Lim, float *Rre,
+                         float *Rim, int ldm, float *gnorm2, cudaStream_t st);
+// A[n][s] = scale * |sum_m conj(L_nm) R_sm|^2 with unit diagonal, zero padding to lda.
+cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm,
+                            int M, int S, float scale, void *A, int lda, int a_dtype, cudaStream_t st);
+// b_n = scale * Re(L_n^H C L_n) for n < S.
+cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,
+                       float *b, cudaStream_t st);
+cudaError_t launch_wavelet(const float *b, int nx, int ny, int levels, int pred, int eps_mode, float eps_abs,
+                           float eps_rel, long long keep_K, int32_t *idx, int32_t *S_sub, float *detail,
+                           float *eps_abs_out, float *work_absd, cudaStream_t st);
+cudaError_t launch_gather(const float *src, const int32_t *idx, int n, float *dst, cudaStream_t st);
+cudaError_t launch_scatter_power(const float *x_sub, const int32_t *idx, const float *gnorm2, int n,
+                                 float *x_full, int S, double *total, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProduct), written with
+// round-to-nearest intrinsics so that no contraction changes them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+#endif

@@ -1,0 +1,81 @@
+// Mean-square DAS map (§2 Eq. (2)): b_n = scale * Re(l_n^H C l_n).
+//
+// Each warp takes grid points one after another: the point's vector l_n is put
+// in shared memory, lane p forms (C l_n)_p for p = lane, lane+32, ... from the
+// CTA's copy of C, multiplies by conj(l_np) and the warp sums.  C is staged in
+// chunks of rows so any M <= 256 fits in shared memory.  FP32 arithmetic.
+#include "common.cuh"
+
+namespace {
+
+constexpr int DAS_THREADS = 256, DAS_WARPS = DAS_THREADS / 32, ROWS_PER_CHUNK = 64;
+
+__global__ void __launch_bounds__(DAS_THREADS) das_kernel(const float *__restrict__ Lre, const float *__restrict__ Lim,
+                                                          int ldm, int M, int S, const float2 *__restrict__ C,
+                                                          float scale, float *__restrict__ b, int pts_per_warp) {
+    extern __shared__ float2 sm[];
+    const int cstride = M + 1;                       // padded row stride of the C chunk (float2)
+    float2 *sC = sm;                                 // ROWS_PER_CHUNK x cstride
+    float2 *sl = sm + ROWS_PER_CHUNK * cstride;      // DAS_WARPS x pts_per_warp x M
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = (blockIdx.x * DAS_WARPS + warp) * pts_per_warp;
+
+    // stage this warp's point vectors
+    for (int q = 0; q < pts_per_warp; ++q) {
+        const int n = base + q;
+        float2 *dst = sl + (size_t)(warp * pts_per_warp + q) * M;
+        for (int m = lane; m < M; m += 32)
+            dst[m] = (n < S) ? make_float2(Lre[(size_t)n * ldm + m], Lim[(size_t)n * ldm + m]) : make_float2(0.f, 0.f);
+    }
+    float acc[16];
+    for (int q = 0; q < pts_per_warp; ++q) acc[q] = 0.f;
+
+    for (int p0 = 0; p0 < M; p0 += ROWS_PER_CHUNK) {
+        const int rows = min(ROWS_PER_CHUNK, M - p0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * M; e += DAS_THREADS) {
+            const int r = e / M, c = e % M;
+            sC[r * cstride + c] = C[(size_t)(p0 + r) * M + c];
+        }
+        __syncthreads();
+        for (int q = 0; q < pts_per_warp; ++q) {
+            const float2 *l = sl + (size_t)(warp * pts_per_warp + q) * M;
+            float a = acc[q];
+            for (int r = lane; r < rows; r += 32) {
+                const float2 *crow = sC + r * cstride;
+                float yr = 0.f, yi = 0.f;
+                for (int c = 0; c < M; ++c) {
+                    const float2 cv = crow[c], lv = l[c];
+                    yr = fmaf(cv.x, lv.x, fmaf(-cv.y, lv.y, yr));
+                    yi = fmaf(cv.x, lv.y, fmaf(cv.y, lv.x, yi));
+                }
+                const float2 lp = l[p0 + r];
+                // Re(conj(l_p) * y_p) = lr*yr + li*yi
+                a = fmaf(lp.x, yr, fmaf(lp.y, yi, a));
+            }
+            acc[q] = a;
+        }
+    }
+    for (int q = 0; q < pts_per_warp; ++q) {
+        float v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int n = base + q;
+        if (lane == 0 && n < S) b[n] = scale * v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,
+                       float *b, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const int ppw = M <= 64 ? 8 : 4;
+    const size_t smem = sizeof(float2) * ((size_t)ROWS_PER_CHUNK * (M + 1) + (size_t)DAS_WARPS * ppw * M);
+    cudaError_t e = cudaFuncSetAttribute(das_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int pts_per_cta = DAS_WARPS * ppw;
+    const int blocks = (S + pts_per_cta - 1) / pts_per_cta;
+    das_kernel<<<blocks, DAS_THREADS, smem, st>>>(Lre, Lim, ldm, M, S, (const float2 *)C, scale, b, ppw);
+    return cudaGetLastError();
+}

@@ -1,0 +1,31 @@
+// Descriptors of the persistent Gauss-Seidel launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct SweepSys {
+    const void *A;     // S x lda, FP32 or BF16
+    const float *b;    // S
+    float *x;          // S, in/out
+    float *state;      // 2*S or nullptr
+    float *dbuf;       // nb*32 exchanged dx
+    unsigned *flags;   // nb block flags: (epoch << 1) | active
+    int lda, S, dtype, init, iters;
+    int cta0, ncta, rows_per_cta, resident;
+    unsigned epoch0;
+};
+
+constexpr int SWEEP_MAX_SYS = 24;
+
+struct SweepParams {
+    SweepSys sys[SWEEP_MAX_SYS];
+    int nsys;
+    int *status;
+    unsigned long long *active_blocks;
+    unsigned long long timeout_ns;
+    int withhold_block;  // test hook: block index never published, or -1
+};
+
+size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident);
+cudaError_t sweep_occupancy(size_t smem, int *blocks_per_sm);
+cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream_t st);

@@ -1,0 +1,228 @@
+"""Python binding of libdamas.so: the C-ABI entry points under the same names.
+
+Each function marshals torch tensors (device memory) into the C call and
+checks the status; every computation runs in the library's CUDA kernels.
+PyTorch provides device memory and streams only.  There is no CPU path: the
+functions raise when the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (BF16, EPS_ABS, EPS_KEEP_FRAC, EPS_REL_MAX, F32, FORM_E, FORM_P, INIT_STATE, INIT_X,  # noqa: F401
+                   INIT_ZERO, PRED_HAAR, PRED_LINEAR)
+
+
+class DamasError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_lib.ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor required")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor required")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (damas_create / damas_destroy)."""
+
+    def __init__(self, device: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.lib = _lib.load()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.damas_create(ctypes.byref(h), device)
+        if rc != 0:
+            raise DamasError(rc, "damas_create failed")
+        self.handle = h
+
+    def check(self, rc: int):
+        if rc != 0:
+            raise DamasError(rc, self.lib.damas_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.damas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Geometry:
+    """Array and scan grid (§2): microphone positions on the device plus grid parameters."""
+    mic_xyz: torch.Tensor  # (M, 3) float64 on the device
+    nx: int
+    ny: int
+    x0: float
+    y0: float
+    dx: float
+    dy: float
+    z: float
+    c: float = 343.0
+    formulation: int = FORM_E
+
+    @property
+    def M(self):
+        return int(self.mic_xyz.shape[0])
+
+    @property
+    def S(self):
+        return self.nx * self.ny
+
+    def cstruct(self) -> _lib.damas_geom:
+        return _lib.damas_geom(self.M, self.mic_xyz.data_ptr(), self.nx, self.ny, self.x0, self.y0, self.dx, self.dy,
+                               self.z, self.c, self.formulation)
+
+    @staticmethod
+    def from_scene(mics: np.ndarray, grid, c: float, formulation: int = FORM_E, device="cuda") -> "Geometry":
+        m = torch.as_tensor(np.ascontiguousarray(mics, dtype=np.float64), device=device)
+        return Geometry(m, grid.nx, grid.ny, grid.x0, grid.y0, grid.dx, grid.dy, grid.z, c, formulation)
+
+
+def damas_lda(S: int) -> int:
+    return _lib.load().damas_lda(int(S))
+
+
+def damas_build_psf(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor | None = None, S_sub: int | None = None,
+                    a_dtype: int = F32, A: torch.Tensor | None = None, gnorm2: torch.Tensor | None = None,
+                    stream=None):
+    """PSF matrix A (S_sub x lda) of the selected points; returns (A, gnorm2)."""
+    S_sub = geom.S if idx is None and S_sub is None else (S_sub if S_sub is not None else int(idx.numel()))
+    lda = damas_lda(S_sub)
+    dt = torch.float32 if a_dtype == F32 else torch.bfloat16
+    if A is None:
+        A = torch.empty((S_sub, lda), dtype=dt, device=geom.mic_xyz.device)
+    if gnorm2 is None:
+        gnorm2 = torch.empty(S_sub, dtype=torch.float32, device=geom.mic_xyz.device)
+    g = geom.cstruct()
+    ctx.check(ctx.lib.damas_build_psf(ctx.handle, ctypes.byref(g), float(freq), _ptr(idx), int(S_sub), int(a_dtype),
+                                      _ptr(A), int(A.shape[1]), _ptr(gnorm2), _stream(stream)))
+    return A, gnorm2
+
+
+def das_map(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, b: torch.Tensor | None = None, stream=None):
+    """DAS map of Eq. (2) on the full grid; C is (M, M, 2) float32 (re, im)."""
+    if b is None:
+        b = torch.empty(geom.S, dtype=torch.float32, device=C.device)
+    g = geom.cstruct()
+    ctx.check(ctx.lib.das_map(ctx.handle, ctypes.byref(g), float(freq), _ptr(C), _ptr(b), _stream(stream)))
+    return b
+
+
+def wavelet_compress_grid(ctx: Context, b: torch.Tensor, nx: int, ny: int, levels: int, predictor: int = PRED_HAAR,
+                          eps_mode: int = EPS_KEEP_FRAC, eps: float = 0.1, idx: torch.Tensor | None = None,
+                          S_sub: torch.Tensor | None = None, detail: torch.Tensor | None = None,
+                          eps_abs: torch.Tensor | None = None, stream=None):
+    """Algorithm 1.  Returns (idx capacity tensor, S_sub device tensor, detail, eps_abs)."""
+    dev = b.device
+    idx = torch.empty(nx * ny, dtype=torch.int32, device=dev) if idx is None else idx
+    S_sub = torch.empty(1, dtype=torch.int32, device=dev) if S_sub is None else S_sub
+    cfg = _lib.damas_wavelet_cfg(int(levels), int(predictor), int(eps_mode), float(eps))
+    ctx.check(ctx.lib.wavelet_compress_grid(ctx.handle, _ptr(b), int(nx), int(ny), ctypes.byref(cfg), _ptr(idx),
+                                            _ptr(S_sub), _ptr(detail), _ptr(eps_abs), _stream(stream)))
+    return idx, S_sub, detail, eps_abs
+
+
+def damas_gather(ctx: Context, src: torch.Tensor, idx: torch.Tensor, n: int, dst: torch.Tensor | None = None,
+                 stream=None):
+    dst = torch.empty(n, dtype=torch.float32, device=src.device) if dst is None else dst
+    ctx.check(ctx.lib.damas_gather(ctx.handle, _ptr(src), _ptr(idx), int(n), _ptr(dst), _stream(stream)))
+    return dst
+
+
+def damas_scatter_power(ctx: Context, x_sub: torch.Tensor, idx: torch.Tensor | None, gnorm2: torch.Tensor | None,
+                        n: int, S: int, x_full: torch.Tensor | None = None, total: torch.Tensor | None = None,
+                        stream=None):
+    dev = x_sub.device
+    x_full = torch.empty(S, dtype=torch.float32, device=dev) if x_full is None else x_full
+    total = torch.empty(1, dtype=torch.float64, device=dev) if total is None else total
+    ctx.check(ctx.lib.damas_scatter_power(ctx.handle, _ptr(x_sub), _ptr(idx), _ptr(gnorm2), int(n), _ptr(x_full),
+                                          int(S), _ptr(total), _stream(stream)))
+    return x_full, total
+
+
+@dataclass
+class System:
+    """One A x = b system for damas_solve (device tensors)."""
+    A: torch.Tensor
+    b: torch.Tensor
+    x: torch.Tensor
+    iters: int
+    S: int | None = None
+    state: torch.Tensor | None = None
+    init: int = INIT_ZERO
+
+    def cstruct(self) -> _lib.damas_system:
+        S = self.S if self.S is not None else int(self.b.numel())
+        dt = F32 if self.A.dtype == torch.float32 else BF16
+        return _lib.damas_system(self.A.data_ptr(), dt, int(self.A.shape[1]), S, self.b.data_ptr(), self.x.data_ptr(),
+                                 self.state.data_ptr() if self.state is not None else None, int(self.init),
+                                 int(self.iters))
+
+
+def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int = 0,
+                status: torch.Tensor | None = None, withhold_block: int = 0, stream=None):
+    """DAMAS Gauss-Seidel sweeps (Eq. (13)-(14)) on a batch of systems in one persistent launch."""
+    if isinstance(systems, System):
+        systems = [systems]
+    arr = (_lib.damas_system * len(systems))(*[s.cstruct() for s in systems])
+    cfg = _lib.damas_solve_cfg(int(ctas_per_system), int(timeout_ms),
+                               status.data_ptr() if status is not None else None, int(withhold_block))
+    ctx.check(ctx.lib.damas_solve(ctx.handle, arr, len(systems), ctypes.byref(cfg), _stream(stream)))
+    return systems
+
+
+# ----------------------------------------------------------------------------- one frequency bin
+def solve_bin(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, iters: int, compressed: bool = True,
+              levels: int = 2, predictor: int = PRED_HAAR, eps_mode: int = EPS_KEEP_FRAC, eps: float = 0.1,
+              a_dtype: int = F32, stream=None):
+    """The method for one bin (§5): DAS map, wavelet-compressed grid (Algorithm 1),
+    PSF matrix of the kept points, Gauss-Seidel from x = 0, power map on the
+    full grid.  One host synchronisation reads the compressed size."""
+    b = das_map(ctx, geom, freq, C, stream=stream)
+    if compressed:
+        idx, S_sub_t, _, _ = wavelet_compress_grid(ctx, b, geom.nx, geom.ny, levels, predictor, eps_mode, eps,
+                                                   stream=stream)
+        S_sub = int(S_sub_t.item())
+        idx = idx[:S_sub]
+        b_sub = damas_gather(ctx, b, idx, S_sub, stream=stream)
+    else:
+        idx, S_sub, b_sub = None, geom.S, b
+    A, g2 = damas_build_psf(ctx, geom, freq, idx, S_sub, a_dtype, stream=stream)
+    x = torch.empty(S_sub, dtype=torch.float32, device=b.device)
+    damas_solve(ctx, System(A, b_sub, x, iters), stream=stream)
+    x_full, total = damas_scatter_power(ctx, x, idx, g2 if geom.formulation == FORM_E else None, S_sub, geom.S,
+                                        stream=stream)
+    return {"b": b, "idx": idx, "S_sub": S_sub, "A": A, "gnorm2": g2, "b_sub": b_sub, "x_sub": x, "x": x_full,
+            "total_power": total}
+
+
+def csm_tensor(C: np.ndarray, device="cuda") -> torch.Tensor:
+    """M x M complex CSM as the (M, M, 2) float32 device tensor das_map takes."""
+    out = np.empty(C.shape + (2,), np.float32)
+    out[..., 0] = np.real(C)
+    out[..., 1] = np.imag(C)
+    return torch.as_tensor(out, device=device)

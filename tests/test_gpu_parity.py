@@ -1,0 +1,349 @@
+"""GPU parity: every hot-path step through the C-ABI library against the oracle.
+
+Tolerances (the numbers are derived in the design notes):
+  - A (FP32): max |A_gpu - A_oracle| <= 5e-6 (entries lie in [0, 1]; FP32 vectors
+    and an FP32 Gram of M terms); BF16 storage: relative 2^-8 per entry.
+  - DAS map: max |b_gpu - b| <= 2e-5 * max |b|.
+  - Compressed grid: bit-exact indices, count and threshold on an identical FP32 map.
+  - Sweeps, identical FP32 inputs: ||x_gpu - x_oracle||_2 <= 1e-4 ||x_oracle||_2
+    after the same number of sweeps (the oracle iterates in FP64 on the same A, b).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_1608_05179_gb300")
+D = P.damas
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = D.Context(0)
+    yield c
+    c.close()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def geom_of(sc, form=O.FORM_E):
+    return D.Geometry.from_scene(sc.mics, sc.grid, sc.c, form)
+
+
+def padded(A64, dtype=torch.float32):
+    S = A64.shape[0]
+    lda = D.damas_lda(S)
+    out = np.zeros((S, lda), np.float32)
+    out[:, :S] = A64
+    return torch.as_tensor(out).to("cuda", dtype)
+
+
+# ----------------------------------------------------------------------------- a1 + a4
+@pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
+def test_psf_full_grid_matches_oracle(ctx, form):
+    sc = synth.scene_monopole_small()
+    g = geom_of(sc, form)
+    A, g2 = D.damas_build_psf(ctx, g, sc.freq)
+    torch.cuda.synchronize()
+    Ao, g2o = O.psf_matrix(sc.mics, sc.grid.points(), sc.freq, sc.c, form)
+    Ag = A.cpu().numpy()
+    S = sc.grid.S
+    assert np.abs(Ag[:, :S] - Ao).max() <= 5e-6
+    assert np.all(np.diag(Ag) == 1.0)
+    assert np.all(Ag[:, S:] == 0.0)
+    assert np.allclose(g2.cpu().numpy(), g2o, rtol=1e-6)
+
+
+def test_psf_selected_points_and_bf16(ctx):
+    sc = synth.scene_spiral_81()
+    g = geom_of(sc)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(sc.grid.S, 333, replace=False)).astype(np.int32)
+    it = torch.as_tensor(idx, device="cuda")
+    A, g2 = D.damas_build_psf(ctx, g, sc.freq, it, len(idx))
+    Ab, _ = D.damas_build_psf(ctx, g, sc.freq, it, len(idx), a_dtype=D.BF16)
+    torch.cuda.synchronize()
+    Ao, g2o = O.psf_matrix(sc.mics, sc.grid.points()[idx], sc.freq, sc.c)
+    assert np.abs(A.cpu().numpy()[:, :333] - Ao).max() <= 5e-6
+    Abf = Ab.float().cpu().numpy()[:, :333]
+    assert np.all(np.abs(Abf - Ao) <= 2.0 ** -8 * np.abs(Ao) + 1e-6)
+    assert np.allclose(g2.cpu().numpy(), g2o, rtol=1e-6)
+
+
+# ----------------------------------------------------------------------------- a2
+@pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
+@pytest.mark.parametrize("which", ["small", "spiral"])
+def test_das_map_matches_oracle(ctx, form, which):
+    sc = synth.scene_monopole_small() if which == "small" else synth.scene_spiral_81()
+    b = D.das_map(ctx, geom_of(sc, form), sc.freq, D.csm_tensor(sc.C))
+    torch.cuda.synchronize()
+    bo = O.das_map(sc.mics, sc.grid.points(), sc.freq, sc.c, sc.C, form)
+    assert np.abs(b.cpu().numpy() - bo).max() <= 2e-5 * np.abs(bo).max()
+
+
+def test_das_map_large_array(ctx):
+    rng = np.random.default_rng(4)
+    sc = synth.scene_random(rng, 128, 41, 3, 5000.0)
+    b = D.das_map(ctx, geom_of(sc), sc.freq, D.csm_tensor(sc.C))
+    torch.cuda.synchronize()
+    bo = O.das_map(sc.mics, sc.grid.points(), sc.freq, sc.c, sc.C)
+    assert np.abs(b.cpu().numpy() - bo).max() <= 2e-5 * np.abs(bo).max()
+
+
+# ----------------------------------------------------------------------------- a3
+WAVELET_CASES = [
+    # (scene, N, levels, predictor, mode, eps)
+    ("spiral", 81, 2, O.PRED_HAAR, O.EPS_KEEP_FRAC, 0.10),
+    ("spiral", 81, 4, O.PRED_LINEAR, O.EPS_REL_MAX, 0.05),
+    ("spiral", 81, 4, O.PRED_HAAR, O.EPS_ABS, 0.5),
+    ("spiral", 81, 2, O.PRED_LINEAR, O.EPS_KEEP_FRAC, 0.30),
+    ("spiral", 81, 2, O.PRED_LINEAR, O.EPS_KEEP_FRAC, 0.02),
+    ("spiral", 81, 2, O.PRED_LINEAR, O.EPS_KEEP_FRAC, 1.0),
+    ("paper50", 50, 5, O.PRED_LINEAR, O.EPS_REL_MAX, 0.1),
+    ("paper50", 50, 5, O.PRED_HAAR, O.EPS_KEEP_FRAC, 0.07),
+    ("small", 21, 2, O.PRED_LINEAR, O.EPS_REL_MAX, 0.01),
+    ("rect", 0, 3, O.PRED_LINEAR, O.EPS_KEEP_FRAC, 0.15),
+]
+
+
+def _wavelet_map(which):
+    if which == "spiral":
+        sc = synth.scene_spiral_81()
+        return O.das_map(sc.mics, sc.grid.points(), sc.freq, sc.c, sc.C).astype(np.float32), 81, 81
+    if which == "small":
+        sc = synth.scene_monopole_small()
+        return O.das_map(sc.mics, sc.grid.points(), sc.freq, sc.c, sc.C).astype(np.float32), 21, 21
+    if which == "paper50":
+        mics = synth.mic_disc(60, 0.5, np.random.default_rng(0))
+        g = synth.square_plane(50, 5.77, 5.0)
+        C = synth.simulate_csm(mics, np.array([g.point(24, 24)]), np.array([1.0]), 3000.0, 340.0, 15.0,
+                               np.random.default_rng(1))
+        return O.das_map(mics, g.points(), 3000.0, 340.0, C).astype(np.float32), 50, 50
+    rng = np.random.default_rng(9)                       # rectangular grid with a ragged edge
+    return rng.random(37 * 70).astype(np.float32), 70, 37
+
+
+@pytest.mark.parametrize("case", WAVELET_CASES)
+def test_wavelet_bit_exact(ctx, case):
+    which, _, L, pred, mode, eps = case
+    b, nx, ny = _wavelet_map(which)
+    bt = torch.as_tensor(b, device="cuda")
+    det = torch.empty(nx * ny, dtype=torch.float32, device="cuda")
+    ea = torch.empty(1, dtype=torch.float32, device="cuda")
+    idx, n, _, _ = D.wavelet_compress_grid(ctx, bt, nx, ny, L, pred, mode, eps, detail=det, eps_abs=ea)
+    torch.cuda.synchronize()
+    io, do, lo, eo = O.wavelet_select(b, nx, ny, L, pred, mode, eps)
+    n = int(n.item())
+    assert n == len(io)
+    assert np.array_equal(idx[:n].cpu().numpy(), io)
+    assert np.array_equal(det.cpu().numpy().view(np.uint32), do.view(np.uint32))
+    assert ea.item() == eo or (math.isinf(eo) and math.isinf(ea.item()))
+
+
+def test_wavelet_ties_and_constant(ctx):
+    for b in (np.zeros((21, 21), np.float32), np.tile(np.float32([1, 0]), (33, 17))[:, :33].copy()):
+        ny, nx = b.shape
+        bt = torch.as_tensor(b.reshape(-1), device="cuda")
+        for mode, eps in ((O.EPS_KEEP_FRAC, 0.1), (O.EPS_ABS, 0.0), (O.EPS_REL_MAX, 0.5)):
+            idx, n, _, _ = D.wavelet_compress_grid(ctx, bt, nx, ny, 2, O.PRED_LINEAR, mode, eps)
+            io, _, _, _ = O.wavelet_select(b, nx, ny, 2, O.PRED_LINEAR, mode, eps)
+            assert np.array_equal(idx[:int(n.item())].cpu().numpy(), io)
+
+
+# ----------------------------------------------------------------------------- a5, a7
+def test_gather_and_scatter_power(ctx):
+    rng = np.random.default_rng(3)
+    S = 1000
+    b = rng.random(S).astype(np.float32)
+    idx = np.sort(rng.choice(S, 77, replace=False)).astype(np.int32)
+    it = torch.as_tensor(idx, device="cuda")
+    sub = D.damas_gather(ctx, torch.as_tensor(b, device="cuda"), it, 77)
+    assert np.array_equal(sub.cpu().numpy(), b[idx])
+    g2 = (1.0 + rng.random(77)).astype(np.float32)
+    xf, tot = D.damas_scatter_power(ctx, sub, it, torch.as_tensor(g2, device="cuda"), 77, S)
+    ref = O.scatter(O.to_power(b[idx].astype(np.float64), g2.astype(np.float64)), idx, S)
+    assert np.allclose(xf.cpu().numpy(), ref, rtol=1e-7)
+    assert abs(tot.item() - ref.sum()) <= 1e-6 * ref.sum()
+
+
+# ----------------------------------------------------------------------------- a6
+def _solve_gpu(ctx, A64, b64, iters, dtype=torch.float32, **kw):
+    S = len(b64)
+    A = padded(A64, dtype)
+    b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+    x = torch.zeros(S, dtype=torch.float32, device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x, iters), **kw)
+    return x.cpu().numpy()
+
+
+def _oracle_fp32_inputs(A64, b64, iters, bf16=False):
+    if bf16:
+        A32 = torch.as_tensor(A64.astype(np.float32)).to(torch.bfloat16).float().numpy()
+    else:
+        A32 = A64.astype(np.float32)
+    return O.gauss_seidel(A32.astype(np.float64), b64.astype(np.float32).astype(np.float64), iters)
+
+
+def _compressed_system():
+    sc = synth.scene_spiral_81()
+    pts = sc.grid.points()
+    b = O.das_map(sc.mics, pts, sc.freq, sc.c, sc.C)
+    idx, _, _, _ = O.wavelet_select(b.astype(np.float32), 81, 81, 2, O.PRED_HAAR, O.EPS_KEEP_FRAC, 0.1)
+    A, _ = O.psf_matrix(sc.mics, pts[idx], sc.freq, sc.c)
+    return A, b[idx]
+
+
+@pytest.mark.parametrize("ctas", [0, 1, 3, 7])
+def test_sweep_small_full_grid(ctx, ctas):
+    sc = synth.scene_monopole_small()
+    pts = sc.grid.points()
+    A, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c)
+    b = O.das_map(sc.mics, pts, sc.freq, sc.c, sc.C)
+    x = _solve_gpu(ctx, A, b, 100, ctas_per_system=ctas)
+    xo = _oracle_fp32_inputs(A, b, 100)
+    assert rel_l2(x, xo) <= 1e-4
+
+
+@pytest.mark.parametrize("ctas", [0, 2, 5])
+def test_sweep_compressed_1000(ctx, ctas):
+    A, b = _compressed_system()
+    x = _solve_gpu(ctx, A, b, 1000, ctas_per_system=ctas)
+    xo = _oracle_fp32_inputs(A, b, 1000)
+    assert rel_l2(x, xo) <= 1e-4
+
+
+@pytest.mark.parametrize("S", [1, 5, 31, 32, 33, 95, 257])
+def test_sweep_ragged_sizes(ctx, S):
+    A, b = synth.random_psd_system(np.random.default_rng(S), S)
+    for ctas in (0, 2):
+        x = _solve_gpu(ctx, A, b, 60, ctas_per_system=ctas)
+        xo = _oracle_fp32_inputs(A, b, 60)
+        assert rel_l2(x, xo) <= 1e-4, (S, ctas)
+
+
+def test_sweep_bf16_storage(ctx):
+    """BF16-stored A: parity with the oracle iterating on the same BF16-rounded A.
+    (Against the FP32 trajectory the iterate differs by far more than the
+    rounding: the system is singular and the iteration follows a different path
+    through the solution set, which the precision study quantifies.)"""
+    A, b = _compressed_system()
+    x = _solve_gpu(ctx, A, b, 500, dtype=torch.bfloat16)
+    assert rel_l2(x, _oracle_fp32_inputs(A, b, 500, bf16=True)) <= 1e-4
+
+
+def test_sweep_zero_rhs_and_zero_iters(ctx):
+    A, _ = synth.random_psd_system(np.random.default_rng(1), 100)
+    x = _solve_gpu(ctx, A, np.zeros(100), 10)
+    assert np.all(x == 0)
+    A2, b2 = synth.random_psd_system(np.random.default_rng(2), 70)
+    assert np.all(_solve_gpu(ctx, A2, b2, 0) == 0)
+
+
+def test_sweep_resume_is_bit_exact_and_deterministic(ctx):
+    A64, b64 = _compressed_system()
+    S = len(b64)
+    A = padded(A64)
+    b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+    x1 = torch.zeros(S, device="cuda")
+    st = torch.zeros(2 * S, device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x1, 300, state=st), ctas_per_system=4)
+    D.damas_solve(ctx, D.System(A, b, x1, 200, state=st, init=D.INIT_STATE), ctas_per_system=4)
+    x2 = torch.zeros(S, device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x2, 500), ctas_per_system=4)
+    x3 = torch.zeros(S, device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x3, 500), ctas_per_system=4)
+    assert torch.equal(x1, x2) and torch.equal(x2, x3)
+
+
+def test_sweep_warm_start_from_x(ctx):
+    A64, b64 = _compressed_system()
+    S = len(b64)
+    xo_half = _oracle_fp32_inputs(A64, b64, 200)
+    A = padded(A64)
+    b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+    x = torch.as_tensor(xo_half.astype(np.float32), device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x, 300, init=D.INIT_X), ctas_per_system=3)
+    xo = O.gauss_seidel(A64.astype(np.float32).astype(np.float64), b64.astype(np.float32).astype(np.float64), 300,
+                        x0=xo_half.astype(np.float32).astype(np.float64))
+    assert rel_l2(x.cpu().numpy(), xo) <= 1e-4
+
+
+def test_batched_systems_equal_solo(ctx):
+    rng = np.random.default_rng(11)
+    systems, solo = [], []
+    for S in (40, 257, 600, 96):
+        A64, b64 = synth.random_psd_system(rng, S)
+        A = padded(A64)
+        b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+        systems.append(D.System(A, b, torch.zeros(S, device="cuda"), 150))
+        solo.append(D.System(A, b, torch.zeros(S, device="cuda"), 150))
+    D.damas_solve(ctx, systems)
+    for s in solo:
+        D.damas_solve(ctx, s)
+    for a, s in zip(systems, solo):
+        assert torch.equal(a.x, s.x)
+
+
+def test_sweep_wait_timeout_reports_status_and_context_survives(ctx):
+    """A withheld block flag makes the other CTAs' bounded waits run out: the
+    call reports DAMAS_ETIMEDOUT, no GPU fault, and the next solve is correct."""
+    A64, b64 = synth.random_psd_system(np.random.default_rng(5), 200)
+    with pytest.raises(D.DamasError) as ei:
+        _solve_gpu(ctx, A64, b64, 20, ctas_per_system=3, timeout_ms=200, withhold_block=1)
+    assert ei.value.code == D._lib.DAMAS_ETIMEDOUT
+    x = _solve_gpu(ctx, A64, b64, 20, ctas_per_system=3)
+    assert rel_l2(x, _oracle_fp32_inputs(A64, b64, 20)) <= 1e-4
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _solve_gpu(ctx, A64, b64, 5, ctas_per_system=3, timeout_ms=100, withhold_block=2, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == D._lib.DAMAS_ETIMEDOUT
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    A, b = synth.random_psd_system(np.random.default_rng(0), 40)
+    At = padded(A)
+    bt = torch.as_tensor(b.astype(np.float32), device="cuda")
+    x = torch.zeros(40, device="cuda")
+    with pytest.raises(D.DamasError):
+        D.damas_solve(ctx, D.System(At[:, :40].contiguous(), bt, x, 5))   # lda not a multiple of 32
+    with pytest.raises(D.DamasError):
+        D.damas_solve(ctx, D.System(At, bt, x, 5, init=D.INIT_STATE))     # no state buffer
+    with pytest.raises(D.DamasError):
+        D.wavelet_compress_grid(ctx, bt, 5, 8, 0)                         # levels 0
+
+
+# ----------------------------------------------------------------------------- end to end
+def test_end_to_end_compressed_bin(ctx):
+    """§5 procedure on the 81x81 spiral scene (M=64, 2 kHz, Haar L=2, keep 10%),
+    1000 sweeps: grid selection agrees with the oracle's except for points whose
+    coefficient lies within 1e-5 * max(b) of the threshold; the power map agrees
+    within the trajectory sensitivity of the iteration to FP32-level input changes."""
+    sc = synth.scene_spiral_81()
+    g = geom_of(sc)
+    out = D.solve_bin(ctx, g, sc.freq, D.csm_tensor(sc.C), 1000, compressed=True, levels=2,
+                      predictor=O.PRED_HAAR, eps_mode=O.EPS_KEEP_FRAC, eps=0.1)
+    torch.cuda.synchronize()
+    orc = O.solve_bin(sc.mics, sc.grid, sc.freq, sc.c, sc.C, 1000, compressed=True, levels=2,
+                      predictor=O.PRED_HAAR, eps_mode=O.EPS_KEEP_FRAC, eps=0.1)
+    gi = set(out["idx"].cpu().numpy().tolist())
+    oi = set(orc["idx"].tolist())
+    bo32 = orc["b"].astype(np.float32)
+    _, det, lev, ea = O.wavelet_select(bo32, 81, 81, 2, O.PRED_HAAR, O.EPS_KEEP_FRAC, 0.1)
+    near = {n for n in (gi ^ oi) if abs(abs(det[n]) - ea) <= 1e-5 * bo32.max()}
+    assert gi ^ oi == near
+    if gi == oi:
+        assert rel_l2(out["x"].cpu().numpy(), orc["x"]) <= 2e-3
+    assert abs(out["total_power"].item() - orc["x"].sum()) <= 2e-3 * orc["x"].sum()
