@@ -158,6 +158,33 @@ int wavelet_compress_grid(damas_ctx *ctx, const float *b_dev, int nx, int ny, co
                           int32_t *idx_dev, int32_t *S_sub_dev, float *detail_dev, float *eps_abs_dev,
                           damas_stream stream);
 
+/*
+ * wavelet_compress_grid without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device memory
+ * when they need a compressed grid (a real-time audio thread that must not wait
+ * on the driver's allocator, a plug-in that may only use memory its host
+ * application gave it, a process whose device-memory budget is fixed at
+ * start-up).  It computes exactly what wavelet_compress_grid computes, from the
+ * same arguments; the caller still provides every input and output buffer.
+ *  - Its one work array is a file-scope device array of DAMAS_NOALLOC_MAX_POINTS
+ *    floats (1 MiB) inside libdamas.so; every device that loads the library holds
+ *    it until the process exits.  Grids with more than DAMAS_NOALLOC_MAX_POINTS
+ *    points are rejected with DAMAS_EINVAL and nothing is enqueued.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, under a lock, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call on a device uses the same array, which keeps whatever the last
+ *    call left there (nothing in it has to start at zero: each call writes every
+ *    entry it reads).  Calls whose work overlaps on the GPU (different streams,
+ *    or different host threads) race on it: serialise them.
+ *  - ctx supplies the device and receives the error message; no context scratch
+ *    is used.
+ */
+#define DAMAS_NOALLOC_MAX_POINTS 262144
+int wavelet_compress_grid_noalloc(damas_ctx *ctx, const float *b_dev, int nx, int ny, const damas_wavelet_cfg *cfg,
+                                  int32_t *idx_dev, int32_t *S_sub_dev, float *detail_dev, float *eps_abs_dev,
+                                  damas_stream stream);
+
 /* ------------------------------------------------------------------ a5, a7: restriction and scatter */
 
 /* dst[i] = src[idx[i]], i < n (b~ of Eq. (24)). */

@@ -50,6 +50,8 @@ SIGNATURES = {
     "das_map": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_void_p, c_void_p]),
     "wavelet_compress_grid": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(damas_wavelet_cfg), c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wavelet_compress_grid_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(damas_wavelet_cfg),
+                                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "damas_gather": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "damas_scatter_power": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
                                     c_void_p]),

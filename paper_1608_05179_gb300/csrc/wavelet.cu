@@ -237,3 +237,82 @@ cudaError_t launch_scatter_power(const float *x_sub, const int32_t *idx, const f
     scatter_power_kernel<<<1, ST, 0, st>>>(x_sub, idx, gnorm2, n, x_full, S, total);
     return cudaGetLastError();
 }
+
+// ----------------------------------------------------------------------------- allocation-free variant
+// Some callers cannot allocate device memory at the moment they need a
+// compressed grid: a real-time audio thread must not wait on the driver's
+// allocator, a plug-in hosted by another application may only touch memory the
+// host application handed it, and code that runs under a fixed device-memory
+// budget reserved at start-up may not grow it.  wavelet_compress_grid_noalloc
+// serves them: the one work array the selection needs lives in the file-scope
+// device array below, created when the library's module is loaded on a device
+// and held by every device that loads the library until the process exits.
+#include <mutex>
+
+namespace {
+
+// |detail| per grid point (work array of the selection kernel).
+static __device__ __align__(256) float g_noalloc_absd[DAMAS_NOALLOC_MAX_POINTS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" int wavelet_compress_grid_noalloc(damas_ctx *ctx, const float *b_dev, int nx, int ny,
+                                             const damas_wavelet_cfg *cfg, int32_t *idx_dev, int32_t *S_sub_dev,
+                                             float *detail_dev, float *eps_abs_dev, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (!cfg) return ctx_fail(ctx, DAMAS_EINVAL, "cfg is NULL");
+    if (!b_dev || !idx_dev || !S_sub_dev) return ctx_fail(ctx, DAMAS_EINVAL, "b_dev, idx_dev, S_sub_dev are required");
+    if (nx < 1 || ny < 1 || (long long)nx * ny > DAMAS_NOALLOC_MAX_POINTS)
+        return ctx_fail(ctx, DAMAS_EINVAL, "grid %dx%d exceeds the %d points of the allocation-free work array", nx, ny,
+                        DAMAS_NOALLOC_MAX_POINTS);
+    if (cfg->levels < 1 || cfg->levels > 15) return ctx_fail(ctx, DAMAS_EINVAL, "levels=%d out of range", cfg->levels);
+    if (cfg->predictor != DAMAS_PRED_LINEAR && cfg->predictor != DAMAS_PRED_HAAR)
+        return ctx_fail(ctx, DAMAS_EINVAL, "unknown predictor");
+    if (cfg->eps_mode < DAMAS_EPS_ABS || cfg->eps_mode > DAMAS_EPS_KEEP_FRAC)
+        return ctx_fail(ctx, DAMAS_EINVAL, "unknown eps_mode");
+    if (!(cfg->eps >= 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "eps must be >= 0");
+    if (cfg->eps_mode == DAMAS_EPS_KEEP_FRAC && cfg->eps > 1.0)
+        return ctx_fail(ctx, DAMAS_EINVAL, "keep fraction must be in [0, 1]");
+    if (ctx->device < 0 || ctx->device >= kMaxDevices) return ctx_fail(ctx, DAMAS_EINVAL, "device index too large");
+
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) {
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    }
+    int rc = DAMAS_OK;
+    float *work = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side name of
+        // the array is only a stand-in, its device address comes from the runtime
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[ctx->device]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_absd);
+            if (e != cudaSuccess)
+                rc = ctx_fail(ctx, DAMAS_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            else
+                g_noalloc_ptr[ctx->device] = (float *)p;
+        }
+        work = g_noalloc_ptr[ctx->device];
+    }
+    if (rc == DAMAS_OK) {
+        // the work array needs no clearing: the kernel writes every entry it reads
+        const int S = nx * ny;
+        const int J = cfg->levels;
+        const long long n0 = (long long)(((nx - 1) >> J) + 1) * (((ny - 1) >> J) + 1);
+        const long long K =
+            cfg->eps_mode == DAMAS_EPS_KEEP_FRAC ? (long long)ceil(cfg->eps * (double)S) - n0 : 0;
+        cudaError_t e = launch_wavelet(b_dev, nx, ny, J, cfg->predictor, cfg->eps_mode, (float)cfg->eps,
+                                       (float)cfg->eps, K, idx_dev, S_sub_dev, detail_dev, eps_abs_dev, work,
+                                       (cudaStream_t)stream);
+        if (e != cudaSuccess) rc = ctx_fail(ctx, DAMAS_ECUDA, "wavelet launch: %s", cudaGetErrorString(e));
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}

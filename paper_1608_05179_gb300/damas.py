@@ -146,6 +146,27 @@ def wavelet_compress_grid(ctx: Context, b: torch.Tensor, nx: int, ny: int, level
     return idx, S_sub, detail, eps_abs
 
 
+def wavelet_compress_grid_noalloc(ctx: Context, b: torch.Tensor, nx: int, ny: int, levels: int,
+                                  predictor: int = PRED_HAAR, eps_mode: int = EPS_KEEP_FRAC, eps: float = 0.1,
+                                  idx: torch.Tensor | None = None, S_sub: torch.Tensor | None = None,
+                                  detail: torch.Tensor | None = None, eps_abs: torch.Tensor | None = None,
+                                  stream=None):
+    """Algorithm 1 through the allocation-free entry point: same results as
+    wavelet_compress_grid, with the library's own fixed device work array instead
+    of context scratch (for callers that cannot allocate device memory when they
+    run, e.g. real-time threads or plug-ins limited to memory their host gave
+    them).  The output tensors passed in are used as given; pass them all to keep
+    the call free of allocations on the Python side too."""
+    dev = b.device
+    idx = torch.empty(nx * ny, dtype=torch.int32, device=dev) if idx is None else idx
+    S_sub = torch.empty(1, dtype=torch.int32, device=dev) if S_sub is None else S_sub
+    cfg = _lib.damas_wavelet_cfg(int(levels), int(predictor), int(eps_mode), float(eps))
+    ctx.check(ctx.lib.wavelet_compress_grid_noalloc(ctx.handle, _ptr(b), int(nx), int(ny), ctypes.byref(cfg),
+                                                    _ptr(idx), _ptr(S_sub), _ptr(detail), _ptr(eps_abs),
+                                                    _stream(stream)))
+    return idx, S_sub, detail, eps_abs
+
+
 def damas_gather(ctx: Context, src: torch.Tensor, idx: torch.Tensor, n: int, dst: torch.Tensor | None = None,
                  stream=None):
     dst = torch.empty(n, dtype=torch.float32, device=src.device) if dst is None else dst
