@@ -215,15 +215,21 @@ enum {
 };
 
 typedef struct {
-    const void *A_dev;  /* S x lda, row-major, FP32 or BF16 (a_dtype), unit diagonal */
+    const void *A_dev;  /* S x lda, row-major, FP32 or BF16 (a_dtype), unit diagonal;
+                           entries >= 0 (PSF matrices are) let rows that cannot move be
+                           skipped exactly; a block with a negative entry is solved in full */
+    const void *At_dev; /* A transposed, same type and lda, or NULL when A is symmetric
+                           (formulation E).  Read when A's rows are not held in shared
+                           memory: column c of A is then read as row c of At */
     int a_dtype;        /* DAMAS_F32 or DAMAS_BF16 */
     int lda;            /* row stride in elements, multiple of 8, >= S */
     int S;              /* number of unknowns, >= 1 */
     const float *b_dev; /* device float[S] */
     float *x_dev;       /* device float[S], in/out */
-    float *state_dev;   /* optional device float[2*S]: the residual as an unevaluated
-                           FP32 pair (hi, lo); written at the end of every solve,
-                           read with DAMAS_INIT_STATE */
+    float *state_dev;   /* optional device float[2*S + 64]: the iteration's internal state
+                           (residual as an FP32 pair hi/lo plus the last two blocks of
+                           dx not yet folded into every row); opaque, written at the
+                           end of every solve, read with DAMAS_INIT_STATE */
     int init;           /* DAMAS_INIT_* */
     int iters;          /* number of sweeps T >= 0 */
 } damas_system;
@@ -233,6 +239,9 @@ typedef struct {
     int timeout_ms;       /* bound on every device-side wait, default (0) 2000 ms */
     int32_t *status_dev;  /* optional device int32[1]: receives DAMAS_OK or DAMAS_ETIMEDOUT;
                              when given the call does not synchronise */
+    int a_placement;      /* 0 = automatic; 1 = keep each CTA's rows of A in shared memory
+                             (DAMAS_EINVAL if they do not fit); 2 = stream A tiles from
+                             global memory (L2/HBM) through a shared-memory ring */
     int withhold_block;   /* test hook for the bounded waits, 0 in normal use: when > 0 the
                              owner of row block (withhold_block - 1) never publishes it, so
                              the waits of the other CTAs for it run out */
@@ -244,10 +253,11 @@ typedef struct {
  *   r_i = sum_{j<i} A_ij x_j^(n+1) + sum_{j>=i} A_ij x_j^(n) - b_i,
  *   x_i = max(x_i - r_i / A_ii, 0),  with A_ii = 1.
  * The row order is exactly the paper's.  Rows are processed in blocks of 32:
- * a block is solved sequentially on chip from its residual, then the change of
- * x is applied to the residual of every other row (A[:,J] dx_J).  The residual
- * is carried as an FP32 (hi, lo) pair updated with error-free transformations,
- * so it does not drift over thousands of sweeps.
+ * a block is solved sequentially on chip from its residual, and the change of
+ * x is applied to the residual of every other row (A[:,J] dx_J) while the next
+ * block is being solved.  The residual is carried as an FP32 (hi, lo) pair
+ * updated with error-free transformations, so it does not drift over thousands
+ * of sweeps.
  *   sys    host array of nsys descriptors (copied before the call returns).
  *   cfg    optional (NULL = defaults).
  * Each system is solved by a team of CTAs that run concurrently (a cooperative

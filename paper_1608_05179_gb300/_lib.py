@@ -30,13 +30,14 @@ class damas_wavelet_cfg(ctypes.Structure):
 
 
 class damas_system(ctypes.Structure):
-    _fields_ = [("A_dev", c_void_p), ("a_dtype", c_int), ("lda", c_int), ("S", c_int), ("b_dev", c_void_p),
+    _fields_ = [("A_dev", c_void_p), ("At_dev", c_void_p), ("a_dtype", c_int), ("lda", c_int), ("S", c_int),
+                ("b_dev", c_void_p),
                 ("x_dev", c_void_p), ("state_dev", c_void_p), ("init", c_int), ("iters", c_int)]
 
 
 class damas_solve_cfg(ctypes.Structure):
     _fields_ = [("ctas_per_system", c_int), ("timeout_ms", c_int), ("status_dev", c_void_p),
-                ("withhold_block", c_int)]
+                ("a_placement", c_int), ("withhold_block", c_int)]
 
 
 # every symbol include/damas.h declares, with its signature

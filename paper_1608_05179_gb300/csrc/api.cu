@@ -241,7 +241,7 @@ struct Plan {
     size_t smem;
 };
 
-Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int cta_budget) {
+Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int placement, int cta_budget) {
     const int nb = (s.S + 31) / 32;
     const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
     Plan p{};
@@ -251,25 +251,29 @@ Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int ct
         p.resident = res ? 1 : 0;
         p.smem = sweep_smem_bytes(R, s.lda, s.a_dtype, res);
     };
-    if (forced > 0) {
-        const int P = std::min(forced, nb);
-        const int R = (nb + P - 1) / P * 32;
-        finish(R, sweep_smem_bytes(R, s.lda, s.a_dtype, true) <= budget);
+    auto rows_for = [&](int P) { return (nb + P - 1) / P * 32; };
+    // the most rows of A a CTA can hold next to its x and residual
+    const size_t per_row = sweep_smem_bytes(1, s.lda, s.a_dtype, true);
+    const int rmax_res = (int)std::min<size_t>(budget / per_row, (size_t)1 << 20) / 32 * 32;
+    if (nb == 1) {  // a single block is always held in shared memory
+        finish(32, true);
         return p;
     }
-    // rows of A that fit in shared memory next to x and the residual
-    const size_t per_row = sweep_smem_bytes(1, s.lda, s.a_dtype, true);
-    const int rmax = (int)std::min<size_t>(budget / per_row, (size_t)1 << 20) / 32 * 32;
-    if (rmax >= 32) {
-        const int P = (nb * 32 + rmax - 1) / rmax;
-        if (P <= cta_budget) {
-            const int R = (nb + P - 1) / P * 32;
-            finish(R, true);
+    if (forced > 0) {
+        const int R = rows_for(std::min(forced, nb));
+        finish(R, placement == 1 || (placement == 0 && R <= rmax_res));
+        return p;
+    }
+    if (placement != 2 && rmax_res >= 32) {
+        const int P = (nb * 32 + rmax_res - 1) / rmax_res;
+        if (P <= std::min(cta_budget, 16) || placement == 1) {
+            finish(rows_for(P), true);
             return p;
         }
     }
-    const int P = std::max(1, std::min(nb, cta_budget));
-    finish((nb + P - 1) / P * 32, false);
+    // rows streamed from global memory: a few hundred rows per CTA
+    const int P = std::max(1, std::min(cta_budget, (nb + 15) / 16));
+    finish(rows_for(P), false);
     return p;
 }
 
@@ -293,6 +297,8 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         if (s.iters < 0 || s.iters > (1 << 24)) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: iters=%d", i, s.iters);
     }
     const int forced = cfg ? cfg->ctas_per_system : 0;
+    const int placement = cfg ? cfg->a_placement : 0;
+    if (placement < 0 || placement > 2) return ctx_fail(ctx, DAMAS_EINVAL, "a_placement=%d", placement);
     const long long timeout_ms = (cfg && cfg->timeout_ms > 0) ? cfg->timeout_ms : 2000;
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -300,7 +306,10 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     // plan every system, then pack them into launches that fit on the device at once
     std::vector<Plan> plans(nsys);
     for (int i = 0; i < nsys; ++i) {
-        plans[i] = plan_system(ctx, sys[i], forced, ctx->sm_count);
+        plans[i] = plan_system(ctx, sys[i], forced, placement, ctx->sm_count);
+        if (plans[i].smem > ctx->smem_optin - 1024)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: %zu bytes of shared memory per CTA do not fit", i,
+                            plans[i].smem);
         int occ = 0;
         cudaError_t e = sweep_occupancy(plans[i].smem, &occ);
         if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
@@ -335,27 +344,20 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         }
         if (!cur.ids.empty()) launches.push_back(cur);
     }
-    // exchange buffers: a flag region (nb words per system) followed by the dx
-    // region (nb*32 floats per system), each sized for the largest launch.  Flag
-    // words only ever hold epoch-tagged flags, so stale ones always compare old.
-    size_t need_flags = 0, need_dx = 0;
+    // exchange buffers: per system nb*32 mailbox words (epoch << 32 | bits(dx)),
+    // sized for the largest launch.  The region only ever holds mailbox words,
+    // and epochs grow from launch to launch, so stale words always read as old.
+    size_t need = 0;
     for (const Launch &L : launches) {
-        size_t f = 0, d = 0;
-        for (int i : L.ids) {
-            const size_t nb = (size_t)(sys[i].S + 31) / 32;
-            f += (size_t)round_up((int)nb, 4) * sizeof(unsigned);
-            d += nb * 32 * sizeof(float);
-        }
-        need_flags = std::max(need_flags, f);
-        need_dx = std::max(need_dx, d);
+        size_t m = 0;
+        for (int i : L.ids) m += (size_t)((sys[i].S + 31) / 32) * 32 * sizeof(unsigned long long);
+        need = std::max(need, m);
     }
-    const size_t flag_bytes = std::max(ctx->solve_flag_bytes, (need_flags + 65535) / 65536 * 65536);
-    const bool relayout = flag_bytes != ctx->solve_flag_bytes || flag_bytes + need_dx > ctx->solve.cap;
-    int rc = ctx_ensure(ctx, ctx->solve, flag_bytes + need_dx);
+    const bool grow = need > ctx->solve.cap;
+    int rc = ctx_ensure(ctx, ctx->solve, need);
     if (rc) return rc;
-    if (relayout) {
+    if (grow) {
         DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->solve.ptr, 0, ctx->solve.cap, st));
-        ctx->solve_flag_bytes = flag_bytes;
         ctx->epoch = 0;
     }
     rc = ctx_ensure(ctx, ctx->status, 64);
@@ -364,7 +366,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
 
     for (const Launch &L : launches) {
-        if ((unsigned long long)ctx->epoch + L.max_iters + 2 >= (1ull << 30)) {
+        if ((unsigned long long)ctx->epoch + L.max_iters + 2 >= 0xffffffffull) {
             DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->solve.ptr, 0, ctx->solve.cap, st));
             ctx->epoch = 0;
         }
@@ -372,11 +374,9 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         memset(&p, 0, sizeof(p));
         p.nsys = (int)L.ids.size();
         p.status = status;
-        p.active_blocks = nullptr;
         p.timeout_ns = (unsigned long long)timeout_ms * 1000000ull;
         p.withhold_block = (cfg && cfg->withhold_block > 0) ? cfg->withhold_block - 1 : -1;
-        char *fl = (char *)ctx->solve.ptr;
-        char *ex = fl + ctx->solve_flag_bytes;
+        unsigned long long *mb = (unsigned long long *)ctx->solve.ptr;
         int cta = 0;
         for (int q = 0; q < p.nsys; ++q) {
             const int i = L.ids[q];
@@ -385,13 +385,12 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
             const int nb = (s.S + 31) / 32;
             SweepSys &d = p.sys[q];
             d.A = s.A_dev;
+            d.At = s.At_dev ? s.At_dev : s.A_dev;
             d.b = s.b_dev;
             d.x = s.x_dev;
             d.state = s.state_dev;
-            d.dbuf = (float *)ex;
-            ex += (size_t)nb * 32 * sizeof(float);
-            d.flags = (unsigned *)fl;
-            fl += (size_t)round_up(nb, 4) * sizeof(unsigned);
+            d.mbox = mb;
+            mb += (size_t)nb * 32;
             d.lda = s.lda;
             d.S = s.S;
             d.dtype = s.a_dtype;

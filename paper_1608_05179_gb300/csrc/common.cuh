@@ -7,7 +7,7 @@
 
 #include <mutex>
 
-#include "../../include/damas.h"
+#include "damas.h"
 
 // ----------------------------------------------------------------------------- context
 struct ScratchBuf {
@@ -26,8 +26,7 @@ struct damas_ctx {
     ScratchBuf solve;    // solver exchange buffers and flags
     ScratchBuf status;   // solver status words
     ScratchBuf misc;
-    unsigned int epoch = 0;      // flag epoch of the solver exchange buffers
-    size_t solve_flag_bytes = 0; // size of the flag region at the start of `solve`
+    unsigned int epoch = 0;      // mailbox epoch of the solver exchange buffers
 };
 
 int ctx_fail(damas_ctx *ctx, int code, const char *fmt, ...);

@@ -1,30 +1,38 @@
 // DAMAS Gauss-Seidel iteration with the non-negativity clamp (§3, Eq. (13)-(14)),
 // as one persistent cooperative launch over a batch of independent systems.
 //
-// Layout: the rows of a system are cut into blocks of 32 (the paper's row order
-// is kept: block J holds rows 32J..32J+31).  A team of `ncta` CTAs serves one
-// system; CTA c owns a contiguous range of blocks (its rows) and keeps, in
-// shared memory, x and the residual r = A x - b of those rows, and its rows of A
-// when they fit (otherwise they are streamed from global memory).
+// Rows are cut into blocks of 32 in the paper's order (block J = rows
+// 32J..32J+31) and processed as the sequence of steps G = t*nb + J (sweep t,
+// block J).  A team of CTAs serves one system: CTA c owns a contiguous range of
+// blocks and keeps x and the residual r = A x - b of its rows in shared memory
+// (r as an unevaluated FP32 pair hi + lo), plus its rows of A when they fit
+// ("resident"); otherwise A is read from global memory (L2/HBM).
 //
-// Sweep, block J in order:
-//  - the owner's warp 0 solves the 32 rows one after another: lane k holds row
-//    k's pending value v_k = x_k - r_k and row k of the 32 x 32 diagonal block of
-//    A in registers; step j broadcasts lane j's v with a shuffle, forms
-//    x_j' = max(v_j, 0) and dx_j = x_j' - x_j, and every lane applies
-//    v_k -= A_kj dx_j (Eq. (13)-(14) with A_jj = 1);
-//  - the owner publishes dx_J (32 floats) and a release flag tagged with the
-//    sweep's epoch; every other CTA of the team waits for that flag (acquire);
-//  - every CTA adds A[rows, J] dx_J to the residual of all of its rows.  The
-//    residual is an unevaluated FP32 pair (hi, lo) and each product and sum goes
-//    through error-free transformations (TwoProduct by FMA, TwoSum), so it does
-//    not drift over thousands of sweeps; the in-block chain above only decides
-//    x and is then discarded.
-// A block whose rows all have x = 0 and r >= 0 cannot change (every step gives
-// dx = 0), so it is skipped exactly, and the flag says so.
-//
-// Every wait is bounded (global timer); a wait that runs out sets the status
-// word to DAMAS_ETIMEDOUT and the whole team returns.
+// Step G, in every CTA of the team (one CTA barrier per step):
+//  - warp 0, if the CTA owns block J, solves its rows in order.  With
+//    w = -r, row j gives dx_j = max(w_j, -x_j) (x_j + dx_j = max(x_j - r_j, 0),
+//    Eq. (14) with A_jj = 1) and every later row i takes w_i -= A_ij dx_j.  A row
+//    with x_j = 0 and w_j + sum_{k<j} A_jk x_k <= 0 cannot move (the earlier rows
+//    of the block can raise w_j by at most that sum, since PSF entries are >= 0
+//    and x_k + dx_k >= 0), so only the remaining "candidate" rows enter the
+//    chain: the lane of row j broadcasts w_j by shuffle and every lane applies
+//    A_kj dx_j.  dx_J is then published as 32 mailbox words
+//    (epoch << 32 | bits(dx)), which carry their own readiness.  Otherwise
+//    warp 0 polls the mailbox of block J (bounded wait).
+//  - warps 1-3 and 5-7, concurrently, fold dx of step G-1 into the residual of
+//    every own row: r_k += sum over the nonzero dx_c of A_kc dx_c, one thread
+//    per row, with error-free transformations (TwoProduct by FMA, TwoSum) so the
+//    residual does not drift over thousands of sweeps.  Entries A_kc of a column
+//    c are read as row c of the transpose (A itself when symmetric), so a warp
+//    reads contiguous memory.  The rows of block J are left alone while warp 0
+//    solves them: warp 0 adds dx_{J-1} to its w itself (a plain FP32 partial
+//    that only steers this block's decisions) and the stored residual of those
+//    rows receives dx_{J-1} one step later, just before dx_J, so every row sees
+//    every dx in step order.  Warp 4 only joins the barriers, leaving warp 0's
+//    scheduler to it.
+// Systems of one block run the same steps without the overlap.  At the end x,
+// the residual and the two dx blocks not yet folded into every row are written
+// out, so a later call continues bit for bit.
 #include "common.cuh"
 
 #include "sweep.cuh"
@@ -32,20 +40,19 @@
 namespace {
 
 constexpr int SW_THREADS = 256;
+constexpr int UPD_WARPS = 6;
+constexpr int UPD_THREADS = 32 * UPD_WARPS;
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ int upd_index(int warp) { return warp < 4 ? warp - 1 : warp - 2; }
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ float ld_relaxed_f32(const float *p) {
-    float v;
-    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
-    return v;
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) {
     int v;
@@ -57,264 +64,494 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ float bf16_bits(unsigned short h) { return __uint_as_float((uint32_t)h << 16); }
 
-// Eight consecutive A entries A[row][col..col+7] as FP32 (col multiple of 8),
-// from shared memory (resident rows) or global memory.  Columns >= S read as 0.
-__device__ __forceinline__ void load8(const SweepSys &s, const char *As, int lds_bytes, bool resident, int row_g,
-                                      int row_l, int col, float a[8]) {
-    if (s.dtype == DAMAS_F32) {
-        const float4 *p = resident ? (const float4 *)(As + (size_t)row_l * lds_bytes + (size_t)col * 4)
-                                   : (const float4 *)((const float *)s.A + (size_t)row_g * s.lda + col);
-        const float4 u = p[0], w = p[1];
-        a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
-        a[4] = w.x; a[5] = w.y; a[6] = w.z; a[7] = w.w;
-    } else {
-        const uint4 *p = resident ? (const uint4 *)(As + (size_t)row_l * lds_bytes + (size_t)col * 2)
-                                  : (const uint4 *)((const __nv_bfloat16 *)s.A + (size_t)row_g * s.lda + col);
-        const uint4 u = p[0];
-        a[0] = bf16_lo(u.x); a[1] = bf16_hi(u.x); a[2] = bf16_lo(u.y); a[3] = bf16_hi(u.y);
-        a[4] = bf16_lo(u.z); a[5] = bf16_hi(u.z); a[6] = bf16_lo(u.w); a[7] = bf16_hi(u.w);
+struct Team {
+    int S, R, nb, row0, nrows, jb0, jb1, lds_w, tile_ld;
+};
+
+// A[row0 + r][c] from the resident copy; the row stride lds_w is an odd number
+// of 32-bit words, so a warp reading one column of 32 rows, or 32 columns of
+// one row, touches 32 different banks.
+template <bool F32>
+__device__ __forceinline__ float res_at(const Team &T, const uint32_t *As, int r, int c) {
+    if (F32) return __uint_as_float(As[r * T.lds_w + c]);
+    const uint32_t w = As[r * T.lds_w + (c >> 1)];
+    return (c & 1) ? bf16_hi(w) : bf16_lo(w);
+}
+// Chain tile of block J for column block X: tile[j][k] = At[32X + j][32J + k] = A[32J + k][32X + j].
+template <bool F32>
+__device__ __forceinline__ float tile_at(const Team &T, const char *tile, int j, int k) {
+    if (F32) return ((const float *)(tile + j * T.tile_ld))[k];
+    return bf16_bits(((const unsigned short *)(tile + j * T.tile_ld))[k]);
+}
+// A[i][col] read as At[col][i] from global memory.
+template <bool F32>
+__device__ __forceinline__ float col_at(const SweepSys &s, int col, int i) {
+    const size_t o = (size_t)col * s.lda + i;
+    if (F32) return ((const float *)s.At)[o];
+    return bf16_bits(((const unsigned short *)s.At)[o]);
+}
+
+// Warp 0: copy the two chain tiles of own block J (diagonal block, and the
+// block of columns J-1) into tile slot `buf`; rows beyond S are zero-filled.
+template <bool F32>
+__device__ __forceinline__ void prefetch_tiles(const SweepSys &s, const Team &T, char *buf, int J) {
+    const int lane = threadIdx.x & 31;
+    const int Jm1 = J == 0 ? T.nb - 1 : J - 1;
+    const int elt = F32 ? 4 : 2;
+    const int lg = F32 ? 3 : 2;  // 16-byte chunks per tile row
+    for (int t = 0; t < 2; ++t) {
+        const int X = t == 0 ? J : Jm1;
+        char *tile = buf + t * 32 * T.tile_ld;
+        for (int e = lane; e < (32 << lg); e += 32) {
+            const int j = e >> lg, q = e & ((1 << lg) - 1);
+            char *dst = tile + j * T.tile_ld + q * 16;
+            const int row = X * 32 + j;
+            if (row < T.S)
+                cp_async16(dst, (const char *)s.At + ((size_t)row * s.lda + (size_t)J * 32) * elt + q * 16);
+            else
+                *(uint4 *)dst = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
-    if (col + 8 > s.S) {
+    cp_async_commit();
+}
+
+// The nonzero entries of a 32-wide dx vector as a compact list (warp 0).
+__device__ __forceinline__ void make_list(float d, unsigned char *idx, int *cnt) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(FULL, d != 0.f);
+    if (d != 0.f) idx[__popc(m & ((1u << lane) - 1u))] = (unsigned char)lane;
+    if (lane == 0) *cnt = __popc(m);
+}
+
+// Compensated sum over the listed columns c of A[row0 + r][c0 + c] * d[c], in
+// list order.  Eight terms at a time, with their loads issued together.
+template <bool F32, bool RES>
+__device__ __forceinline__ void dot_list(const SweepSys &s, const Team &T, const uint32_t *As, int r, int c0,
+                                         const float *d, const unsigned char *idx, int n, float &hi, float &lo) {
+    hi = 0.f;
+    lo = 0.f;
+    for (int q0 = 0; q0 < n; q0 += 8) {
+        int c[8];
+        float a[8], dd[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (col + q >= s.S) a[q] = 0.f;
+        for (int u = 0; u < 8; ++u) c[u] = idx[q0 + u < n ? q0 + u : q0];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            dd[u] = d[c[u]];
+            a[u] = RES ? res_at<F32>(T, As, r, c0 + c[u]) : col_at<F32>(s, c0 + c[u], T.row0 + r);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q0 + u < n) {
+                float p, pe, t;
+                two_prod(a[u], dd[u], p, pe);
+                two_sum(hi, p, hi, t);
+                lo = __fadd_rn(lo, __fadd_rn(t, pe));
+            }
+        }
     }
 }
 
-// r[rows] += A[rows, J0..J0+31] * d[0..31] with compensated accumulation.
-// 4 threads per row, 8 columns each; all threads of the CTA take part.
-__device__ void apply_update(const SweepSys &s, const char *As, int lds_bytes, bool resident, int row0, int nrows,
-                             int J0, const float *dsh, float *rh, float *rl) {
-    const int sub = threadIdx.x & 3;
-    float d[8];
+// residual[r] += (hi + lo), kept as an unevaluated pair
+__device__ __forceinline__ void fold(float *rh, float *rl, int r, float hi, float lo) {
+    float h, t;
+    two_sum(rh[r], hi, h, t);
+    rh[r] = h;
+    rl[r] = __fadd_rn(rl[r], __fadd_rn(lo, t));
+}
+
+// Warp 0 solves own block J.  dm1 (or nullptr) is dx of the previous step
+// (columns of block Jm1), which the stored residual of these rows does not hold
+// yet.  nonneg says that the CTA's diagonal blocks have no negative entry
+// (checked once per launch), which is what lets rows that cannot move be
+// skipped.  Each of the three parts (partial, bound, chain) runs as a dense
+// loop over all 32 positions when many are needed, or walks only the needed
+// ones otherwise (both with warp-uniform control flow).  Returns dx of the
+// lane's row; writes x of the block's rows.
+template <bool F32, bool RES>
+__device__ __forceinline__ float solve_block(const Team &T, const uint32_t *As, const char *tiles, int J, int Jm1,
+                                             float *xs, const float *rh, const float *rl, const float *dm1,
+                                             bool nonneg) {
+    const int k = threadIdx.x & 31;
+    const int i = J * 32 + k, r = i - T.row0;
+    const bool valid = i < T.S;
+    const char *tdiag = tiles, *tpart = tiles + 32 * T.tile_ld;
+    auto diag_at = [&](int j) -> float {
+        return RES ? (valid ? res_at<F32>(T, As, r, J * 32 + j) : 0.f) : tile_at<F32>(T, tdiag, j, k);
+    };
+    auto part_at = [&](int c) -> float {
+        return RES ? (valid ? res_at<F32>(T, As, r, Jm1 * 32 + c) : 0.f) : tile_at<F32>(T, tpart, c, k);
+    };
+    const float x_old = valid ? xs[r] : 0.f;
+    float w = valid ? -__fadd_rn(rh[r], rl[r]) : 0.f;
+
+    // dx of the previous step on this block's rows
+    const unsigned m1 = dm1 ? __ballot_sync(FULL, dm1[k] != 0.f) : 0u;
+    if (__popc(m1) > 6) {
+        float a[32];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) d[q] = dsh[sub * 8 + q];
-    for (int rb = 0; rb < nrows; rb += SW_THREADS / 4) {
-        const int r = rb + (threadIdx.x >> 2);
-        float hi = 0.f, c = 0.f;
-        if (r < nrows) {
-            float a[8];
-            load8(s, As, lds_bytes, resident, row0 + r, r, J0 + sub * 8, a);
-            two_prod(a[0], d[0], hi, c);
+        for (int c = 0; c < 32; ++c) a[c] = part_at(c);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
-            for (int q = 1; q < 8; ++q) {
-                float p, pe, t;
-                two_prod(a[q], d[q], p, pe);
-                two_sum(hi, p, hi, t);
-                c = __fadd_rn(c, __fadd_rn(t, pe));
+        for (int c = 0; c < 32; c += 4) {
+            p0 = __fmaf_rn(a[c], dm1[c], p0);
+            p1 = __fmaf_rn(a[c + 1], dm1[c + 1], p1);
+            p2 = __fmaf_rn(a[c + 2], dm1[c + 2], p2);
+            p3 = __fmaf_rn(a[c + 3], dm1[c + 3], p3);
+        }
+        w = __fsub_rn(w, __fadd_rn(__fadd_rn(p0, p1), __fadd_rn(p2, p3)));
+    } else if (m1) {
+        float p0 = 0.f;
+        unsigned m = m1;
+        while (m) {
+            const int c = __ffs(m) - 1;
+            m &= m - 1u;
+            p0 = __fmaf_rn(part_at(c), dm1[c], p0);
+        }
+        w = __fsub_rn(w, p0);
+    }
+
+    // which rows can move: x > 0, or w + (the most the block's earlier rows can
+    // raise w: sum_{j<k} A_kj x_j) > 0
+    const float *xb = xs + (J * 32 - T.row0);  // x of the block's rows (rows past S read as 0 below)
+    unsigned mask;
+    if (nonneg) {
+        const unsigned mx = __ballot_sync(FULL, valid && x_old > 0.f);
+        float bound = 0.f;
+        if (__popc(mx) > 6) {
+            float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                if (j < k) b0 = __fmaf_rn(diag_at(j), (mx >> j) & 1u ? xb[j] : 0.f, b0);
+                if (j + 1 < k) b1 = __fmaf_rn(diag_at(j + 1), (mx >> (j + 1)) & 1u ? xb[j + 1] : 0.f, b1);
+                if (j + 2 < k) b2 = __fmaf_rn(diag_at(j + 2), (mx >> (j + 2)) & 1u ? xb[j + 2] : 0.f, b2);
+                if (j + 3 < k) b3 = __fmaf_rn(diag_at(j + 3), (mx >> (j + 3)) & 1u ? xb[j + 3] : 0.f, b3);
+            }
+            bound = __fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, b3));
+        } else {
+            unsigned m = mx;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1u;
+                if (j < k) bound = __fmaf_rn(diag_at(j), xb[j], bound);
             }
         }
+        const float margin = 3.8e-6f * (fabsf(w) + bound);
+        mask = __ballot_sync(FULL, valid && (x_old > 0.f || __fadd_rn(w, bound) > -margin));
+    } else {
+        mask = __ballot_sync(FULL, valid);
+    }
+
+    // the rows that can move, in order
+    float dchain = 0.f;
+    if (__popc(mask) > 12) {
+        float arow[32];
 #pragma unroll
-        for (int o = 2; o >= 1; o >>= 1) {
-            const float h2 = __shfl_xor_sync(FULL, hi, o), c2 = __shfl_xor_sync(FULL, c, o);
-            float t;
-            two_sum(hi, h2, hi, t);
-            c = __fadd_rn(__fadd_rn(c, c2), t);
+        for (int j = 0; j < 32; ++j) arow[j] = diag_at(j);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float wj = __shfl_sync(FULL, w, j);
+            const float xj = __shfl_sync(FULL, x_old, j);
+            const float d = fmaxf(wj, -xj);
+            w = __fmaf_rn(-arow[j], d, w);
+            if (k == j) dchain = d;
         }
-        if (sub == 0 && r < nrows) {
-            float h, t;
-            two_sum(rh[r], hi, h, t);
-            rh[r] = h;
-            rl[r] = __fadd_rn(rl[r], __fadd_rn(c, t));
+    } else {
+        unsigned m = mask;
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1u;
+            const float a = diag_at(j);
+            const float wj = __shfl_sync(FULL, w, j);
+            const float d = fmaxf(wj, -xb[j]);
+            w = __fmaf_rn(-a, d, w);
+            if (k == j) dchain = d;
         }
     }
+    const float x_new = __fadd_rn(x_old, dchain);  // = max(x - r, 0)
+    if (valid) xs[r] = x_new;
+    return __fsub_rn(x_new, x_old);
+}
+
+template <bool F32, bool RES>
+__device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &s, float (*dring)[32],
+                                          unsigned char (*nzidx)[32], int *nzcnt, int *s_abort_p, char *smem) {
+    int &s_abort = *s_abort_p;
+    Team T;
+    T.S = s.S;
+    T.R = s.rows_per_cta;
+    T.nb = (s.S + 31) / 32;
+    T.row0 = (blockIdx.x - s.cta0) * T.R;
+    T.nrows = max(0, min(T.R, s.S - T.row0));
+    T.jb0 = T.row0 / 32;
+    T.jb1 = min(T.nb, (T.row0 + T.R) / 32);
+    T.lds_w = (F32 ? s.lda : s.lda / 2) + 1;
+    T.tile_ld = 32 * (F32 ? 4 : 2) + 16;
+    const int S = T.S, nb = T.nb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool pipelined = nb >= 2;
+    const long long Gend = (long long)s.iters * nb;
+    const int elt = F32 ? 4 : 2;
+    bool nonneg_all = true;
+
+    float *rh = (float *)smem;
+    float *rl = rh + T.R;
+    float *xs = rl + T.R;
+    uint32_t *As = (uint32_t *)(xs + T.R);  // resident rows of A
+    char *tiles = (char *)(xs + T.R);       // or: two slots of two chain tiles
+    const int slot_bytes = 2 * 32 * T.tile_ld;
+
+    // ---- prologue
+    if (RES) {
+        const int wpr = s.lda * elt / 4;  // 32-bit words per row of A
+        for (int r = warp; r < T.R; r += SW_THREADS / 32) {
+            const uint32_t *src = (const uint32_t *)((const char *)s.A + (size_t)(T.row0 + r) * s.lda * elt);
+            for (int v = lane; v < wpr; v += 32) As[(size_t)r * T.lds_w + v] = r < T.nrows ? src[v] : 0u;
+        }
+    }
+    int tile_blk0 = -1, tile_blk1 = -1;  // warp 0: the block whose tiles each slot holds
+    if (!RES && warp == 0 && pipelined) {
+        prefetch_tiles<F32>(s, T, tiles, T.jb0);
+        tile_blk0 = T.jb0;
+    }
+    for (int r = threadIdx.x; r < T.R; r += SW_THREADS) {
+        const int i = T.row0 + r;
+        const bool ok = r < T.nrows;
+        xs[r] = (ok && s.init != DAMAS_INIT_ZERO) ? s.x[i] : 0.f;
+        rh[r] = ok ? (s.init == DAMAS_INIT_STATE ? s.state[i] : (s.init == DAMAS_INIT_X ? 0.f : -s.b[i])) : 0.f;
+        rl[r] = (ok && s.init == DAMAS_INIT_STATE) ? s.state[S + i] : 0.f;
+    }
+    if (warp == 0) {
+        // slots 2 and 3: dx of steps -2 and -1, kept in the state of an earlier call
+        const bool have = s.init == DAMAS_INIT_STATE && pipelined;
+        for (int q = 0; q < 4; ++q) {
+            const float d = (have && q >= 2) ? s.state[2 * S + (q - 2) * 32 + lane] : 0.f;
+            dring[q][lane] = d;
+            make_list(d, nzidx[q], &nzcnt[q]);
+        }
+        if (lane == 0) s_abort = 0;
+    }
+    __syncthreads();
+    if (s.init == DAMAS_INIT_X) {
+        // r_i = sum_j A_ij x_j - b_i, compensated; one warp per row
+        for (int r = warp; r < T.nrows; r += SW_THREADS / 32) {
+            float hi = 0.f, lo = 0.f;
+            const char *Arow = (const char *)s.A + (size_t)(T.row0 + r) * s.lda * elt;
+            for (int j = lane; j < S; j += 32) {
+                const float a = F32 ? ((const float *)Arow)[j] : bf16_bits(((const unsigned short *)Arow)[j]);
+                float pr, pe, t;
+                two_prod(a, s.x[j], pr, pe);
+                two_sum(hi, pr, hi, t);
+                lo = __fadd_rn(lo, __fadd_rn(t, pe));
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const float h2 = __shfl_xor_sync(FULL, hi, o), l2 = __shfl_xor_sync(FULL, lo, o);
+                float t;
+                two_sum(hi, h2, hi, t);
+                lo = __fadd_rn(__fadd_rn(lo, l2), t);
+            }
+            if (lane == 0) {
+                float h, t;
+                two_sum(hi, -s.b[T.row0 + r], h, t);
+                rh[r] = h;
+                rl[r] = __fadd_rn(lo, t);
+            }
+        }
+    }
+    // PSF matrices have no negative entry; a CTA whose diagonal blocks do is
+    // solved row by row without skipping
+    {
+        int negs = 0;
+        const char *gA = (const char *)s.A;
+        for (int e = threadIdx.x; e < T.nrows * 32; e += SW_THREADS) {
+            const int r = e >> 5, c = (T.row0 + r) / 32 * 32 + (e & 31);
+            if (c < S) {
+                const size_t o = (size_t)(T.row0 + r) * s.lda + c;
+                const float a = F32 ? ((const float *)gA)[o] : bf16_bits(((const unsigned short *)gA)[o]);
+                negs |= a < 0.f;
+            }
+        }
+        nonneg_all = !__syncthreads_or(negs);
+    }
+    if (warp == 0 && tile_blk0 >= 0) cp_async_wait_all();
+    __syncthreads();
+
+    // ---- steps
+    int J = 0;
+    unsigned epoch = s.epoch0 + 1u;
+    for (long long G = 0; G < Gend; ++G) {
+        const int Jm1 = J == 0 ? nb - 1 : J - 1;
+        const int Jm2 = Jm1 == 0 ? nb - 1 : Jm1 - 1;
+        const bool ownJ = J >= T.jb0 && J < T.jb1;
+        const int gi = (int)(G & 3), g1 = (gi + 3) & 3, g2 = (gi + 2) & 3;
+
+        if (!pipelined) {
+            // a single block: solve, then fold its dx into its own residual
+            if (warp == 0) {
+                const float dk = solve_block<F32, RES>(T, As, tiles, 0, 0, xs, rh, rl, nullptr, nonneg_all);
+                dring[gi][lane] = dk;
+                make_list(dk, nzidx[gi], &nzcnt[gi]);
+            }
+            __syncthreads();
+            if (warp != 0 && warp != 4 && nzcnt[gi]) {
+                const int u = upd_index(warp) * 32 + lane;
+                if (u < T.nrows) {
+                    float hi, lo;
+                    dot_list<F32, RES>(s, T, As, u, 0, dring[gi], nzidx[gi], nzcnt[gi], hi, lo);
+                    fold(rh, rl, u, hi, lo);
+                }
+            }
+            __syncthreads();
+            ++epoch;
+            continue;
+        }
+
+        if (warp == 0) {
+            if (ownJ) {
+                const char *tl = tiles;
+                if (!RES) {
+                    if (tile_blk1 == J) tl = tiles + slot_bytes;
+                    cp_async_wait_all();
+                    __syncwarp();
+                }
+                const float dk = solve_block<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, dring[g1], nonneg_all);
+                if (J != p.withhold_block)
+                    st_relaxed_u64(s.mbox + (size_t)J * 32 + lane,
+                                   ((unsigned long long)epoch << 32) | __float_as_uint(dk));
+                dring[gi][lane] = dk;
+                make_list(dk, nzidx[gi], &nzcnt[gi]);
+                if (!RES) {
+                    // tiles of the next own block, into the other slot
+                    const int Jn = J + 1 < T.jb1 ? J + 1 : T.jb0;
+                    if (Jn != tile_blk0 && Jn != tile_blk1) {
+                        const bool into1 = tile_blk0 == J;
+                        __syncwarp();
+                        prefetch_tiles<F32>(s, T, tiles + (into1 ? slot_bytes : 0), Jn);
+                        if (into1)
+                            tile_blk1 = Jn;
+                        else
+                            tile_blk0 = Jn;
+                    }
+                }
+            } else {
+                const unsigned long long *mb = s.mbox + (size_t)J * 32 + lane;
+                unsigned long long w = 0, t0 = 0;
+                int iter = 0;
+                for (;;) {
+                    w = ld_relaxed_u64(mb);
+                    if (__all_sync(FULL, (unsigned)(w >> 32) >= epoch)) break;
+                    if ((++iter & 31) == 0) {
+                        int bad = 0;
+                        if (lane == 0) {
+                            const unsigned long long now = global_ns();
+                            if (t0 == 0) t0 = now;
+                            if (now - t0 > p.timeout_ns) {
+                                atomicCAS(p.status, 0, DAMAS_ETIMEDOUT);
+                                bad = 1;
+                            }
+                            if (ld_volatile_i32(p.status) != 0) bad = 1;
+                        }
+                        if (__shfl_sync(FULL, bad, 0)) {
+                            if (lane == 0) s_abort = 1;
+                            break;
+                        }
+                    }
+                }
+                const float d = __uint_as_float((unsigned)w);
+                dring[gi][lane] = d;
+                make_list(d, nzidx[gi], &nzcnt[gi]);
+            }
+        } else if (warp != 4) {
+            const int n1 = nzcnt[g1];
+            const bool ownJm1 = Jm1 >= T.jb0 && Jm1 < T.jb1;
+            const int n2 = ownJm1 ? nzcnt[g2] : 0;
+            if (n1 || n2) {
+                const int skip0 = ownJ ? J * 32 - T.row0 : -64;     // rows of block J: warp 0 has them
+                const int def0 = ownJm1 ? Jm1 * 32 - T.row0 : -64;  // rows of block J-1: fold dx_{G-2} first
+                for (int r = upd_index(warp) * 32 + lane; r < T.nrows; r += UPD_THREADS) {
+                    if (r >= skip0 && r < skip0 + 32) continue;
+                    float hi, lo;
+                    if (n2 && r >= def0 && r < def0 + 32) {
+                        dot_list<F32, RES>(s, T, As, r, Jm2 * 32, dring[g2], nzidx[g2], n2, hi, lo);
+                        fold(rh, rl, r, hi, lo);
+                    }
+                    if (n1) {
+                        dot_list<F32, RES>(s, T, As, r, Jm1 * 32, dring[g1], nzidx[g1], n1, hi, lo);
+                        fold(rh, rl, r, hi, lo);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (warp == 0 && !RES) cp_async_wait_all();  // no copy may land after exit
+            return;
+        }
+        if (++J == nb) {
+            J = 0;
+            ++epoch;
+        }
+    }
+
+    // ---- results: x, and the state a later call continues from
+    for (int r = threadIdx.x; r < T.nrows; r += SW_THREADS) {
+        s.x[T.row0 + r] = xs[r];
+        if (s.state) {
+            s.state[T.row0 + r] = rh[r];
+            s.state[S + T.row0 + r] = rl[r];
+        }
+    }
+    if (s.state && T.jb1 == nb && threadIdx.x < 64) {
+        const long long G = Gend - 2 + (threadIdx.x >> 5);
+        s.state[2 * S + threadIdx.x] = pipelined ? dring[G & 3][lane] : 0.f;
+    }
+    if (warp == 0 && !RES) cp_async_wait_all();
 }
 
 __global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepParams p) {
     extern __shared__ __align__(16) char smem[];
-    __shared__ float dsh[32];
-    __shared__ int s_ctrl[2];  // [0] abort, [1] active
-
-    // which system / team rank
+    __shared__ float dring[4][32];
+    __shared__ unsigned char nzidx[4][32];
+    __shared__ int nzcnt[4];
+    __shared__ int s_abort;
     int si = 0;
     while (si + 1 < p.nsys && (int)blockIdx.x >= p.sys[si + 1].cta0) ++si;
     const SweepSys s = p.sys[si];
-    const int c = blockIdx.x - s.cta0;
-    const int S = s.S;
-    const int R = s.rows_per_cta;
-    const int nb = (S + 31) / 32;
-    const int row0 = c * R;
-    const int nrows = max(0, min(R, S - row0));
-    const int jb0 = row0 / 32, jb1 = min(nb, (row0 + R) / 32);
-    const bool resident = s.resident != 0;
-    const int elt = s.dtype == DAMAS_F32 ? 4 : 2;
-    const int lds_bytes = s.lda * elt + 16;
-
-    float *rh = (float *)smem;
-    float *rl = rh + R;
-    float *xs = rl + R;
-    char *As = (char *)(xs + R);
-
-    // ---- initial state
-    if (resident) {
-        const int vec_per_row = s.lda * elt / 16;
-        for (int e = threadIdx.x; e < nrows * vec_per_row; e += SW_THREADS) {
-            const int r = e / vec_per_row, v = e % vec_per_row;
-            const uint4 *src = (const uint4 *)((const char *)s.A + ((size_t)(row0 + r) * s.lda) * elt) + v;
-            *((uint4 *)(As + (size_t)r * lds_bytes) + v) = *src;
-        }
+    // one specialised body per storage type and placement, chosen once per CTA
+    if (s.dtype == DAMAS_F32) {
+        if (s.resident)
+            sweep_cta<true, true>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+        else
+            sweep_cta<true, false>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+    } else {
+        if (s.resident)
+            sweep_cta<false, true>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+        else
+            sweep_cta<false, false>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
     }
-    for (int r = threadIdx.x; r < R; r += SW_THREADS) {
-        const int i = row0 + r;
-        const bool ok = r < nrows;
-        if (s.init == DAMAS_INIT_STATE) {
-            xs[r] = ok ? s.x[i] : 0.f;
-            rh[r] = ok ? s.state[i] : 0.f;
-            rl[r] = ok ? s.state[S + i] : 0.f;
-        } else if (s.init == DAMAS_INIT_X) {
-            xs[r] = ok ? s.x[i] : 0.f;
-            rh[r] = 0.f;
-            rl[r] = 0.f;
-        } else {
-            xs[r] = 0.f;
-            rh[r] = ok ? -s.b[i] : 0.f;
-            rl[r] = 0.f;
-        }
-    }
-    if (threadIdx.x == 0) s_ctrl[0] = 0;
-    __syncthreads();
-    if (s.init == DAMAS_INIT_X) {
-        // r_i = sum_j A_ij x_j - b_i, compensated; one warp per row
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int r = warp; r < nrows; r += SW_THREADS / 32) {
-            const int i = row0 + r;
-            float hi = 0.f, cc = 0.f;
-            for (int j0 = lane * 8; j0 < S; j0 += 256) {
-                float a[8];
-                load8(s, As, lds_bytes, false, i, r, j0, a);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float xj = (j0 + q < S) ? s.x[j0 + q] : 0.f;
-                    float pr, pe, t;
-                    two_prod(a[q], xj, pr, pe);
-                    two_sum(hi, pr, hi, t);
-                    cc = __fadd_rn(cc, __fadd_rn(t, pe));
-                }
-            }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                const float h2 = __shfl_xor_sync(FULL, hi, o), c2 = __shfl_xor_sync(FULL, cc, o);
-                float t;
-                two_sum(hi, h2, hi, t);
-                cc = __fadd_rn(__fadd_rn(cc, c2), t);
-            }
-            if (lane == 0) {
-                float h, t;
-                two_sum(hi, -s.b[i], h, t);
-                rh[r] = h;
-                rl[r] = __fadd_rn(cc, t);
-            }
-        }
-        __syncthreads();
-    }
-
-    unsigned long long active_count = 0;
-    const int lane = threadIdx.x & 31;
-    for (int t = 0; t < s.iters; ++t) {
-        const unsigned epoch = s.epoch0 + (unsigned)t + 1u;
-        for (int J = 0; J < nb; ++J) {
-            const int J0 = J * 32;
-            const bool own = J >= jb0 && J < jb1;
-            if (own) {
-                if (threadIdx.x < 32) {
-                    const int k = lane, i = J0 + k, r = i - row0;
-                    const bool valid = i < S;
-                    const float x_old = valid ? xs[r] : 0.f;
-                    const float res = valid ? __fadd_rn(rh[r], rl[r]) : 0.f;
-                    float v = __fsub_rn(x_old, res);
-                    const bool quiet = !valid || (x_old == 0.f && v <= 0.f);
-                    const bool active = !__all_sync(FULL, quiet);
-                    float dk = 0.f;
-                    if (active) {
-                        float arow[32];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (valid) {
-                                load8(s, As, lds_bytes, resident, i, r, J0 + 8 * q, arow + 8 * q);
-                            } else {
-#pragma unroll
-                                for (int u = 0; u < 8; ++u) arow[8 * q + u] = 0.f;
-                            }
-                        }
-                        float x_new = x_old;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float vj = __shfl_sync(FULL, v, j);
-                            const float xj = __shfl_sync(FULL, x_old, j);
-                            const float xnj = fmaxf(vj, 0.f);
-                            const float dj = __fsub_rn(xnj, xj);
-                            v = __fmaf_rn(-arow[j], dj, v);
-                            if (k == j) {
-                                x_new = xnj;
-                                dk = dj;
-                            }
-                        }
-                        if (valid) xs[r] = x_new;
-                        s.dbuf[i] = dk;
-                        dsh[k] = dk;
-                    }
-                    __syncwarp();
-                    if (k == 0) {
-                        // the release store orders the warp's dx stores (made
-                        // visible to lane 0 by the warp barrier) before the flag
-                        if (active) ++active_count;
-                        if (J != p.withhold_block) st_release_u32(s.flags + J, (epoch << 1) | (active ? 1u : 0u));
-                        s_ctrl[1] = active ? 1 : 0;
-                    }
-                }
-                __syncthreads();
-            } else {
-                if (threadIdx.x == 0) {
-                    const unsigned long long t0 = global_ns();
-                    int abort = 0, act = 0;
-                    for (;;) {
-                        const unsigned f = ld_acquire_u32(s.flags + J);
-                        if ((f >> 1) >= epoch) {
-                            act = (int)(f & 1u);
-                            break;
-                        }
-                        if (ld_volatile_i32(p.status) != 0) {
-                            abort = 1;
-                            break;
-                        }
-                        if (global_ns() - t0 > p.timeout_ns) {
-                            atomicCAS(p.status, 0, DAMAS_ETIMEDOUT);
-                            abort = 1;
-                            break;
-                        }
-                    }
-                    s_ctrl[0] = abort;
-                    s_ctrl[1] = act;
-                }
-                __syncthreads();
-                if (s_ctrl[0]) return;
-                if (s_ctrl[1] && threadIdx.x < 32) dsh[threadIdx.x] = ld_relaxed_f32(s.dbuf + J0 + threadIdx.x);
-                __syncthreads();
-            }
-            if (s_ctrl[1]) apply_update(s, As, lds_bytes, resident, row0, nrows, J0, dsh, rh, rl);
-            __syncthreads();
-        }
-    }
-
-    for (int r = threadIdx.x; r < nrows; r += SW_THREADS) {
-        s.x[row0 + r] = xs[r];
-        if (s.state) {
-            s.state[row0 + r] = rh[r];
-            s.state[S + row0 + r] = rl[r];
-        }
-    }
-    if (threadIdx.x == 0 && p.active_blocks && active_count) atomicAdd(p.active_blocks, active_count);
 }
 
 }  // namespace
 
 size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident) {
+    const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
     size_t b = (size_t)3 * R * sizeof(float);
-    if (resident) b += (size_t)R * ((size_t)lda * (dtype == DAMAS_F32 ? 4 : 2) + 16);
+    if (resident)
+        b += (size_t)R * ((size_t)lda * elt / 4 + 1) * 4;
+    else
+        b += (size_t)2 * 2 * 32 * (32 * elt + 16);
     return b;
 }
 

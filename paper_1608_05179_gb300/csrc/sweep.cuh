@@ -4,12 +4,12 @@
 #include <stdint.h>
 
 struct SweepSys {
-    const void *A;     // S x lda, FP32 or BF16
-    const float *b;    // S
-    float *x;          // S, in/out
-    float *state;      // 2*S or nullptr
-    float *dbuf;       // nb*32 exchanged dx
-    unsigned *flags;   // nb block flags: (epoch << 1) | active
+    const void *A;            // S x lda, FP32 or BF16
+    const void *At;           // A transposed (same lda), or A itself when A is symmetric
+    const float *b;           // S
+    float *x;                 // S, in/out
+    float *state;             // 2*S + 64 or nullptr: residual (hi, lo) and the two pending dx blocks
+    unsigned long long *mbox; // nb*32 mailbox words: (epoch << 32) | bits(dx)
     int lda, S, dtype, init, iters;
     int cta0, ncta, rows_per_cta, resident;
     unsigned epoch0;
@@ -21,11 +21,11 @@ struct SweepParams {
     SweepSys sys[SWEEP_MAX_SYS];
     int nsys;
     int *status;
-    unsigned long long *active_blocks;
     unsigned long long timeout_ns;
     int withhold_block;  // test hook: block index never published, or -1
 };
 
+// shared memory a CTA needs for R rows (resident: its rows of A; otherwise chain tiles only)
 size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident);
 cudaError_t sweep_occupancy(size_t smem, int *blocks_per_sm);
 cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream_t st);

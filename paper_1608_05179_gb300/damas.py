@@ -195,23 +195,30 @@ class System:
     S: int | None = None
     state: torch.Tensor | None = None
     init: int = INIT_ZERO
+    At: torch.Tensor | None = None  # transpose of A; None when A is symmetric
 
     def cstruct(self) -> _lib.damas_system:
         S = self.S if self.S is not None else int(self.b.numel())
         dt = F32 if self.A.dtype == torch.float32 else BF16
-        return _lib.damas_system(self.A.data_ptr(), dt, int(self.A.shape[1]), S, self.b.data_ptr(), self.x.data_ptr(),
+        return _lib.damas_system(self.A.data_ptr(), self.At.data_ptr() if self.At is not None else None, dt,
+                                 int(self.A.shape[1]), S, self.b.data_ptr(), self.x.data_ptr(),
                                  self.state.data_ptr() if self.state is not None else None, int(self.init),
                                  int(self.iters))
 
 
+PLACE_AUTO, PLACE_RESIDENT, PLACE_STREAM = 0, 1, 2
+
+
 def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int = 0,
-                status: torch.Tensor | None = None, withhold_block: int = 0, stream=None):
+                status: torch.Tensor | None = None, a_placement: int = PLACE_AUTO, withhold_block: int = 0,
+                stream=None):
     """DAMAS Gauss-Seidel sweeps (Eq. (13)-(14)) on a batch of systems in one persistent launch."""
     if isinstance(systems, System):
         systems = [systems]
     arr = (_lib.damas_system * len(systems))(*[s.cstruct() for s in systems])
     cfg = _lib.damas_solve_cfg(int(ctas_per_system), int(timeout_ms),
-                               status.data_ptr() if status is not None else None, int(withhold_block))
+                               status.data_ptr() if status is not None else None, int(a_placement),
+                               int(withhold_block))
     ctx.check(ctx.lib.damas_solve(ctx.handle, arr, len(systems), ctypes.byref(cfg), _stream(stream)))
     return systems
 

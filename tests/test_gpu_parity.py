@@ -217,10 +217,10 @@ def test_sweep_small_full_grid(ctx, ctas):
     assert rel_l2(x, xo) <= 1e-4
 
 
-@pytest.mark.parametrize("ctas", [0, 2, 5])
-def test_sweep_compressed_1000(ctx, ctas):
+@pytest.mark.parametrize("ctas,place", [(0, 0), (11, 1), (1, 2), (1, 0), (2, 2), (5, 2), (0, 2)])
+def test_sweep_compressed_1000(ctx, ctas, place):
     A, b = _compressed_system()
-    x = _solve_gpu(ctx, A, b, 1000, ctas_per_system=ctas)
+    x = _solve_gpu(ctx, A, b, 1000, ctas_per_system=ctas, a_placement=place)
     xo = _oracle_fp32_inputs(A, b, 1000)
     assert rel_l2(x, xo) <= 1e-4
 
@@ -228,10 +228,10 @@ def test_sweep_compressed_1000(ctx, ctas):
 @pytest.mark.parametrize("S", [1, 5, 31, 32, 33, 95, 257])
 def test_sweep_ragged_sizes(ctx, S):
     A, b = synth.random_psd_system(np.random.default_rng(S), S)
-    for ctas in (0, 2):
-        x = _solve_gpu(ctx, A, b, 60, ctas_per_system=ctas)
-        xo = _oracle_fp32_inputs(A, b, 60)
-        assert rel_l2(x, xo) <= 1e-4, (S, ctas)
+    xo = _oracle_fp32_inputs(A, b, 60)
+    for ctas, place in ((0, 0), (2, 0), (0, 2), (3, 2)):
+        x = _solve_gpu(ctx, A, b, 60, ctas_per_system=ctas, a_placement=place)
+        assert rel_l2(x, xo) <= 1e-4, (S, ctas, place)
 
 
 def test_sweep_bf16_storage(ctx):
@@ -244,6 +244,39 @@ def test_sweep_bf16_storage(ctx):
     assert rel_l2(x, _oracle_fp32_inputs(A, b, 500, bf16=True)) <= 1e-4
 
 
+@pytest.mark.parametrize("ctas,place", [(5, 1), (3, 2), (1, 2)])
+def test_sweep_nonsymmetric_with_transpose(ctx, ctas, place):
+    """Formulation P gives a non-symmetric A: the solver reads its columns through
+    the transpose when A's rows are streamed, and from shared memory otherwise."""
+    sc = synth.scene_monopole_small()
+    pts = sc.grid.points()
+    A64, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c, O.FORM_P)
+    b64 = O.das_map(sc.mics, pts, sc.freq, sc.c, sc.C, O.FORM_P)
+    S = len(b64)
+    A = padded(A64)
+    At = padded(np.ascontiguousarray(A64.T))
+    b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+    x = torch.zeros(S, device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x, 100, At=At), ctas_per_system=ctas, a_placement=place)
+    assert rel_l2(x.cpu().numpy(), _oracle_fp32_inputs(A64, b64, 100)) <= 1e-4
+
+
+def test_sweep_negative_entries_solved_in_full(ctx):
+    """Rows are skipped only when A >= 0 guarantees they cannot move; a matrix with
+    negative entries is solved row by row (still the same iteration)."""
+    rng = np.random.default_rng(8)
+    S = 150
+    Y = rng.standard_normal((S, 2 * S))
+    A64 = Y @ Y.T / (2 * S)
+    dg = np.sqrt(np.diag(A64))
+    A64 = A64 / dg[:, None] / dg[None, :]
+    np.fill_diagonal(A64, 1.0)
+    b64 = A64 @ np.abs(rng.standard_normal(S)) * (rng.random(S) < 0.3)
+    for ctas, place in ((0, 0), (2, 2)):
+        x = _solve_gpu(ctx, A64, b64, 80, ctas_per_system=ctas, a_placement=place)
+        assert rel_l2(x, _oracle_fp32_inputs(A64, b64, 80)) <= 1e-4
+
+
 def test_sweep_zero_rhs_and_zero_iters(ctx):
     A, _ = synth.random_psd_system(np.random.default_rng(1), 100)
     x = _solve_gpu(ctx, A, np.zeros(100), 10)
@@ -252,19 +285,22 @@ def test_sweep_zero_rhs_and_zero_iters(ctx):
     assert np.all(_solve_gpu(ctx, A2, b2, 0) == 0)
 
 
-def test_sweep_resume_is_bit_exact_and_deterministic(ctx):
+@pytest.mark.parametrize("ctas,place", [(4, 0), (11, 1), (3, 2)])
+def test_sweep_resume_is_bit_exact_and_deterministic(ctx, ctas, place):
+    """300 + 200 sweeps through the saved state equal 500 sweeps bit for bit, whatever
+    the team layout of the second call; repeated runs are bit-identical."""
     A64, b64 = _compressed_system()
     S = len(b64)
     A = padded(A64)
     b = torch.as_tensor(b64.astype(np.float32), device="cuda")
     x1 = torch.zeros(S, device="cuda")
-    st = torch.zeros(2 * S, device="cuda")
-    D.damas_solve(ctx, D.System(A, b, x1, 300, state=st), ctas_per_system=4)
-    D.damas_solve(ctx, D.System(A, b, x1, 200, state=st, init=D.INIT_STATE), ctas_per_system=4)
+    st = torch.zeros(2 * S + 64, device="cuda")
+    D.damas_solve(ctx, D.System(A, b, x1, 300, state=st), ctas_per_system=ctas, a_placement=place)
+    D.damas_solve(ctx, D.System(A, b, x1, 200, state=st, init=D.INIT_STATE), ctas_per_system=2, a_placement=2)
     x2 = torch.zeros(S, device="cuda")
-    D.damas_solve(ctx, D.System(A, b, x2, 500), ctas_per_system=4)
+    D.damas_solve(ctx, D.System(A, b, x2, 500), ctas_per_system=ctas, a_placement=place)
     x3 = torch.zeros(S, device="cuda")
-    D.damas_solve(ctx, D.System(A, b, x3, 500), ctas_per_system=4)
+    D.damas_solve(ctx, D.System(A, b, x3, 500), ctas_per_system=5, a_placement=2)
     assert torch.equal(x1, x2) and torch.equal(x2, x3)
 
 
