@@ -232,6 +232,7 @@ typedef struct {
                            end of every solve, read with DAMAS_INIT_STATE */
     int init;           /* DAMAS_INIT_* */
     int iters;          /* number of sweeps T >= 0 */
+    int ctas;           /* CTAs in this system's team; 0 = cfg->ctas_per_system or automatic */
 } damas_system;
 
 typedef struct {

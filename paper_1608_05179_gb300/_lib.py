@@ -32,7 +32,7 @@ class damas_wavelet_cfg(ctypes.Structure):
 class damas_system(ctypes.Structure):
     _fields_ = [("A_dev", c_void_p), ("At_dev", c_void_p), ("a_dtype", c_int), ("lda", c_int), ("S", c_int),
                 ("b_dev", c_void_p),
-                ("x_dev", c_void_p), ("state_dev", c_void_p), ("init", c_int), ("iters", c_int)]
+                ("x_dev", c_void_p), ("state_dev", c_void_p), ("init", c_int), ("iters", c_int), ("ctas", c_int)]
 
 
 class damas_solve_cfg(ctypes.Structure):

@@ -271,8 +271,9 @@ Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int pl
             return p;
         }
     }
-    // rows streamed from global memory: a few hundred rows per CTA
-    const int P = std::max(1, std::min(cta_budget, (nb + 15) / 16));
+    // rows streamed from global memory: two blocks per CTA keeps the per-step
+    // update short next to the row chain
+    const int P = std::max(1, std::min(cta_budget, (nb + 1) / 2));
     finish(rows_for(P), false);
     return p;
 }
@@ -295,6 +296,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         if (s.init == DAMAS_INIT_STATE && !s.state_dev)
             return ctx_fail(ctx, DAMAS_EINVAL, "system %d: INIT_STATE needs state_dev", i);
         if (s.iters < 0 || s.iters > (1 << 24)) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: iters=%d", i, s.iters);
+        if (s.ctas < 0) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: ctas=%d", i, s.ctas);
     }
     const int forced = cfg ? cfg->ctas_per_system : 0;
     const int placement = cfg ? cfg->a_placement : 0;
@@ -306,7 +308,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     // plan every system, then pack them into launches that fit on the device at once
     std::vector<Plan> plans(nsys);
     for (int i = 0; i < nsys; ++i) {
-        plans[i] = plan_system(ctx, sys[i], forced, placement, ctx->sm_count);
+        plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement, ctx->sm_count);
         if (plans[i].smem > ctx->smem_optin - 1024)
             return ctx_fail(ctx, DAMAS_EINVAL, "system %d: %zu bytes of shared memory per CTA do not fit", i,
                             plans[i].smem);

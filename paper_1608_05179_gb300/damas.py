@@ -196,6 +196,7 @@ class System:
     state: torch.Tensor | None = None
     init: int = INIT_ZERO
     At: torch.Tensor | None = None  # transpose of A; None when A is symmetric
+    ctas: int = 0                   # team size; 0 = automatic
 
     def cstruct(self) -> _lib.damas_system:
         S = self.S if self.S is not None else int(self.b.numel())
@@ -203,7 +204,7 @@ class System:
         return _lib.damas_system(self.A.data_ptr(), self.At.data_ptr() if self.At is not None else None, dt,
                                  int(self.A.shape[1]), S, self.b.data_ptr(), self.x.data_ptr(),
                                  self.state.data_ptr() if self.state is not None else None, int(self.init),
-                                 int(self.iters))
+                                 int(self.iters), int(self.ctas))
 
 
 PLACE_AUTO, PLACE_RESIDENT, PLACE_STREAM = 0, 1, 2

@@ -46,7 +46,7 @@ def test_struct_layouts_match_c():
 #include "damas.h"
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(damas_geom), sizeof(damas_wavelet_cfg), sizeof(damas_system), sizeof(damas_solve_cfg));
-  printf("%zu %zu %zu\n", offsetof(damas_geom, formulation), offsetof(damas_system, iters), offsetof(damas_solve_cfg, a_placement));
+  printf("%zu %zu %zu\n", offsetof(damas_geom, formulation), offsetof(damas_system, ctas), offsetof(damas_solve_cfg, a_placement));
   return 0;
 }
 """
@@ -60,7 +60,7 @@ int main(void) {
     offs = [int(v) for v in l2.split()]
     assert sizes == [ctypes.sizeof(_lib.damas_geom), ctypes.sizeof(_lib.damas_wavelet_cfg),
                      ctypes.sizeof(_lib.damas_system), ctypes.sizeof(_lib.damas_solve_cfg)]
-    assert offs == [_lib.damas_geom.formulation.offset, _lib.damas_system.iters.offset,
+    assert offs == [_lib.damas_geom.formulation.offset, _lib.damas_system.ctas.offset,
                     _lib.damas_solve_cfg.a_placement.offset]
 
 

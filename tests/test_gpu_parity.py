@@ -65,6 +65,8 @@ def test_psf_full_grid_matches_oracle(ctx, form):
     assert np.all(np.diag(Ag) == 1.0)
     assert np.all(Ag[:, S:] == 0.0)
     assert np.allclose(g2.cpu().numpy(), g2o, rtol=1e-6)
+    if form == O.FORM_E:
+        assert np.array_equal(Ag[:, :S], Ag[:, :S].T)      # exactly symmetric, as the solver assumes
 
 
 def test_psf_selected_points_and_bf16(ctx):
@@ -78,6 +80,7 @@ def test_psf_selected_points_and_bf16(ctx):
     torch.cuda.synchronize()
     Ao, g2o = O.psf_matrix(sc.mics, sc.grid.points()[idx], sc.freq, sc.c)
     assert np.abs(A.cpu().numpy()[:, :333] - Ao).max() <= 5e-6
+    assert torch.equal(A[:, :333], A[:, :333].T) and torch.equal(Ab[:, :333], Ab[:, :333].T)
     Abf = Ab.float().cpu().numpy()[:, :333]
     assert np.all(np.abs(Abf - Ao) <= 2.0 ** -8 * np.abs(Ao) + 1e-6)
     assert np.allclose(g2.cpu().numpy(), g2o, rtol=1e-6)
