@@ -224,6 +224,19 @@ def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int
     return systems
 
 
+def solve_mixed(ctx: Context, A_bf16: torch.Tensor, A_f32: torch.Tensor, b: torch.Tensor, x: torch.Tensor,
+                iters_bulk: int, iters_refine: int, stream=None, **kw):
+    """Mixed-precision schedule: iters_bulk sweeps with A stored in BF16 (half the
+    bytes per sweep), then iters_refine sweeps with the FP32 A, which restart from
+    the exact FP32 residual of the current x."""
+    if iters_bulk:
+        damas_solve(ctx, System(A_bf16, b, x, iters_bulk, init=INIT_ZERO), stream=stream, **kw)
+    if iters_refine:
+        damas_solve(ctx, System(A_f32, b, x, iters_refine, init=INIT_X if iters_bulk else INIT_ZERO),
+                    stream=stream, **kw)
+    return x
+
+
 # ----------------------------------------------------------------------------- one frequency bin
 def solve_bin(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, iters: int, compressed: bool = True,
               levels: int = 2, predictor: int = PRED_HAAR, eps_mode: int = EPS_KEEP_FRAC, eps: float = 0.1,

@@ -1,0 +1,62 @@
+"""Storage precision of A (BF16 bulk sweeps + FP32 refinement) against the FP64 oracle.
+
+The iteration's solution set is not a point (A is singular), so two runs whose
+A differ in rounding follow different paths through it; what stays put is the
+power the map assigns to each source region.  The test compares that power, in
+dB, per source, on the 161x161 near-field scene compressed to about 10% of its
+points (the oracle's selection is used on both sides)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+D = pytest.importorskip("paper_1608_05179_gb300").damas
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = D.Context(0)
+    yield c
+    c.close()
+
+
+def region_power_db(x_full, grid, src_xyz, radius):
+    pts = grid.points()
+    out = []
+    for s in src_xyz:
+        m = np.linalg.norm(pts[:, :2] - s[None, :2], axis=1) <= radius
+        out.append(10 * np.log10(max(x_full[m].sum(), 1e-30)))
+    return np.array(out)
+
+
+def test_bf16_bulk_with_fp32_refinement_per_source_db(ctx):
+    sc = synth.scene_large_161()
+    pts = sc.grid.points()
+    b = O.das_map(sc.mics, pts, sc.freq, sc.c, sc.C)
+    idx, _, _, _ = O.wavelet_select(b.astype(np.float32), 161, 161, 5, O.PRED_LINEAR, O.EPS_KEEP_FRAC, 0.10)
+    A64, g2 = O.psf_matrix(sc.mics, pts[idx], sc.freq, sc.c)
+    T = 400
+    x_orc = O.to_power(O.gauss_seidel(A64, b[idx], T), g2)
+    S = len(idx)
+    geom = D.Geometry.from_scene(sc.mics, sc.grid, sc.c)
+    it = torch.as_tensor(idx, device="cuda")
+    A32, g2d = D.damas_build_psf(ctx, geom, sc.freq, it, S)
+    Abf, _ = D.damas_build_psf(ctx, geom, sc.freq, it, S, a_dtype=D.BF16)
+    bt = torch.as_tensor(b[idx].astype(np.float32), device="cuda")
+    runs = {}
+    for name, (nb, nr) in {"fp32": (0, T), "bf16": (T, 0), "bf16+fp32": (T - 50, 50)}.items():
+        x = torch.zeros(S, device="cuda")
+        D.solve_mixed(ctx, Abf, A32, bt, x, nb, nr)
+        runs[name] = O.scatter(x.cpu().numpy() / g2d.cpu().numpy(), idx, sc.grid.S)
+    beam = 1.22 * 1.5 * sc.c / (1.5 * sc.freq)      # Rayleigh beamwidth at the plane (§5), z0 = D = 1.5 m
+    ref = region_power_db(O.scatter(x_orc, idx, sc.grid.S), sc.grid, sc.src_xyz, beam / 2)
+    err = {k: np.abs(region_power_db(v, sc.grid, sc.src_xyz, beam / 2) - ref) for k, v in runs.items()}
+    assert err["fp32"].max() <= 0.05, err["fp32"]
+    assert err["bf16+fp32"].max() <= 0.5, err["bf16+fp32"]
+    assert err["bf16+fp32"].max() <= err["bf16"].max() + 1e-6
