@@ -271,6 +271,57 @@ typedef struct {
 int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg,
                 damas_stream stream);
 
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * A request loop with continuous batching: requests arriving while others run
+ * are admitted as device memory and SM slots free up, each in its own stream,
+ * and their kernels overlap on the device.  Each request is one measurement
+ * (one array, one grid, several frequency bins); each bin goes through the
+ * method of §5: DAS map, compressed grid (Algorithm 1) unless wavelet.levels is
+ * 0, PSF matrix, Gauss-Seidel from x = 0, power map.  The result of a request
+ * does not depend on what else is in flight (bit for bit).
+ */
+typedef struct {
+    size_t hbm_budget_bytes; /* device memory the loop may hold for requests; 0 = half the free memory */
+    int max_inflight;        /* requests on the device at once; 0 = 8 */
+    int sm_slots;            /* CTAs that concurrent solves may hold together; 0 = the SM count */
+    int rows_per_cta;        /* solver team size target, rows per CTA; 0 = 1024 */
+} damas_serve_cfg;
+
+typedef struct {
+    int M;                     /* microphones */
+    const double *mic_xyz;     /* HOST, M x 3 (copied at submit) */
+    int nx, ny;
+    double x0, y0, dx, dy, z, c;
+    int formulation;           /* DAMAS_FORM_E (the loop's PSF builds assume it) */
+    int n_bins;
+    const double *freqs;       /* HOST, n_bins frequencies (Hz) */
+    const float *C;            /* HOST, n_bins x M x M x 2 interleaved complex CSMs */
+    damas_wavelet_cfg wavelet; /* compression of every bin; levels = 0 solves the full grid */
+    int iters;                 /* Gauss-Seidel sweeps per bin */
+} damas_request;
+
+typedef struct {
+    int status;                /* DAMAS_OK when done, DAMAS_EBUSY while in flight, or an error */
+    int n_bins, S;
+    const float *x;            /* host, n_bins x S power maps (valid until the ticket is released) */
+    const double *total_power; /* host, n_bins integrated powers */
+    const int *S_sub;          /* host, n_bins compressed sizes */
+    double t_submit, t_admit, t_done; /* seconds on the host steady clock */
+} damas_result;
+
+/* Start the loop's worker thread on ctx's device. */
+int damas_serve_start(damas_ctx *ctx, const damas_serve_cfg *cfg);
+/* Copy a request in and queue it; returns a ticket.  DAMAS_EBUSY when the loop is stopped. */
+int damas_serve_submit(damas_ctx *ctx, const damas_request *req, uint64_t *ticket);
+/* Non-blocking: fills *res; res->status is DAMAS_EBUSY until the request is done. */
+int damas_serve_poll(damas_ctx *ctx, uint64_t ticket, damas_result *res);
+/* Drop a finished request's host results. */
+int damas_serve_release(damas_ctx *ctx, uint64_t ticket);
+/* Finish the requests in flight and stop the worker. */
+int damas_serve_stop(damas_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

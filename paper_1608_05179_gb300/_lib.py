@@ -40,6 +40,24 @@ class damas_solve_cfg(ctypes.Structure):
                 ("a_placement", c_int), ("withhold_block", c_int)]
 
 
+class damas_serve_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", c_int), ("sm_slots", c_int),
+                ("rows_per_cta", c_int)]
+
+
+class damas_request(ctypes.Structure):
+    _fields_ = [("M", c_int), ("mic_xyz", c_void_p), ("nx", c_int), ("ny", c_int), ("x0", c_double),
+                ("y0", c_double), ("dx", c_double), ("dy", c_double), ("z", c_double), ("c", c_double),
+                ("formulation", c_int), ("n_bins", c_int), ("freqs", c_void_p), ("C", c_void_p),
+                ("wavelet", damas_wavelet_cfg), ("iters", c_int)]
+
+
+class damas_result(ctypes.Structure):
+    _fields_ = [("status", c_int), ("n_bins", c_int), ("S", c_int), ("x", ctypes.POINTER(ctypes.c_float)),
+                ("total_power", ctypes.POINTER(c_double)), ("S_sub", ctypes.POINTER(c_int)),
+                ("t_submit", c_double), ("t_admit", c_double), ("t_done", c_double)]
+
+
 # every symbol include/damas.h declares, with its signature
 SIGNATURES = {
     "damas_create": (c_int, [ctypes.POINTER(c_void_p), c_int]),
@@ -57,6 +75,11 @@ SIGNATURES = {
     "damas_scatter_power": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
                                     c_void_p]),
     "damas_solve": (c_int, [c_void_p, ctypes.POINTER(damas_system), c_int, ctypes.POINTER(damas_solve_cfg), c_void_p]),
+    "damas_serve_start": (c_int, [c_void_p, ctypes.POINTER(damas_serve_cfg)]),
+    "damas_serve_submit": (c_int, [c_void_p, ctypes.POINTER(damas_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "damas_serve_poll": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(damas_result)]),
+    "damas_serve_release": (c_int, [c_void_p, ctypes.c_uint64]),
+    "damas_serve_stop": (c_int, [c_void_p]),
 }
 
 _lib = None

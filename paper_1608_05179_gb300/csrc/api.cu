@@ -111,6 +111,7 @@ int damas_create(damas_ctx **out, int device) {
 
 int damas_destroy(damas_ctx *ctx) {
     if (!ctx) return DAMAS_EINVAL;
+    if (ctx->serve) serve_shutdown(ctx);
     {
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();

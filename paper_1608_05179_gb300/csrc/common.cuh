@@ -27,7 +27,9 @@ struct damas_ctx {
     ScratchBuf status;   // solver status words
     ScratchBuf misc;
     unsigned int epoch = 0;      // mailbox epoch of the solver exchange buffers
+    struct ServeState *serve = nullptr;  // serving loop, when started
 };
+void serve_shutdown(damas_ctx *ctx);
 
 int ctx_fail(damas_ctx *ctx, int code, const char *fmt, ...);
 int ctx_ensure(damas_ctx *ctx, ScratchBuf &b, size_t bytes);
