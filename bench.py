@@ -320,6 +320,120 @@ def run_reference(args):
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------- other workloads (opt-in)
+def run_band(args):
+    """64 bins log-spaced 1-8 kHz on a 121x121 grid, each bin compressed (linear
+    prediction, 3 levels, relative threshold 1e-3), 1000 sweeps, all bins in one
+    solve launch replayed from a CUDA graph; FP32 and BF16 storage of A."""
+    import torch
+    from paper_1608_05179_gb300 import band as BD
+    from paper_1608_05179_gb300 import damas as D
+    ctx = D.Context(0)
+    scenes = synth.scene_band_121(n_bins=64)
+    geom = D.Geometry.from_scene(scenes[0].mics, scenes[0].grid, scenes[0].c)
+    freqs = [s.freq for s in scenes]
+    C = torch.stack([D.csm_tensor(s.C) for s in scenes])
+    grids = BD.compress_band(ctx, geom, freqs, C, 3, D.PRED_LINEAR, D.EPS_REL_MAX, 1e-3)
+    grids.S_f = [int(v) for v in grids.S_f_dev.cpu().tolist()]
+    out = {"metric": "band bins/s (64 bins, one solve launch)", "unit": "freq-bins/s", "workload":
+           "band: 64 bins 1-8 kHz, 121x121 grid, M=64 spiral, 5 sources, linear L=3 rel 1e-3, 1000 sweeps",
+           "S_f_min": min(grids.S_f), "S_f_max": max(grids.S_f), "S_f_sum": sum(grids.S_f)}
+    for name, dt, elt in (("f32", D.F32, 4), ("bf16", D.BF16, 2)):
+        bs = BD.BandSolver(ctx, geom, freqs, grids.S_f, 1000, dt, rows_per_cta=args.rows or 1024)
+        bs.capture(grids)
+        for _ in range(2):
+            bs.replay()
+        bs.check()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            bs.replay()
+        e1.record()
+        bs.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        # the solve launch alone
+        systems = bs.systems()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        D.damas_solve(ctx, systems, status=bs.status)
+        s1.record()
+        bs.check()
+        solve_ms = s0.elapsed_time(s1)
+        bytes_ = sum(float(n) * n for n in grids.S_f) * elt * 1000
+        out[name] = {"bins_per_s": round(64 / (ms / 1e3), 2), "ms_per_band": round(ms, 2), "solve_ms": round(solve_ms, 2),
+                     "sweep_gbs": round(bytes_ / (solve_ms / 1e3) / 1e9, 1), "ctas": sum(bs.ctas)}
+    ctx.close()
+    return out
+
+
+def run_large(args):
+    """161x161 near-field grid (S=25921), M=128, 6 kHz: 2000 sweeps with A in BF16
+    then 50 with A in FP32, full grid."""
+    import torch
+    from paper_1608_05179_gb300 import damas as D
+    ctx = D.Context(0)
+    sc = synth.scene_large_161()
+    geom = D.Geometry.from_scene(sc.mics, sc.grid, sc.c)
+    b = D.das_map(ctx, geom, sc.freq, D.csm_tensor(sc.C))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record()
+    A32, g2 = D.damas_build_psf(ctx, geom, sc.freq)
+    ev[1].record()
+    Abf, _ = D.damas_build_psf(ctx, geom, sc.freq, a_dtype=D.BF16)
+    x = torch.zeros(sc.grid.S, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ev[2].record()
+    D.damas_solve(ctx, D.System(Abf, b, x, 2000), status=st)
+    ev[3].record()
+    D.damas_solve(ctx, D.System(A32, b, x, 50, init=D.INIT_X), status=st)
+    ev[4].record()
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    S = sc.grid.S
+    t_bulk, t_ref = ev[2].elapsed_time(ev[3]), ev[3].elapsed_time(ev[4])
+    out = {"metric": "large grid BF16+FP32 sweeps", "workload": "161x161 (S=25921) at 1.5 m, M=128, 6 kHz, 8 sources; "
+           "2000 BF16 + 50 FP32 sweeps, full grid", "psf_f32_ms": round(ev[0].elapsed_time(ev[1]), 2),
+           "bulk_ms": round(t_bulk, 1), "refine_ms": round(t_ref, 1),
+           "bulk_sweep_gbs": round(float(S) * S * 2 * 2000 / (t_bulk / 1e3) / 1e9, 1),
+           "refine_sweep_gbs": round(float(S) * S * 4 * 50 / (t_ref / 1e3) / 1e9, 1)}
+    ctx.close()
+    return out
+
+
+def run_serve(args):
+    """Poisson stream (200 req/s) of independent requests: M in {32,64,128}, grid side
+    in {41,81,121,161}, 1-32 bins in 1-10 kHz, kept fraction 2-30%, 1-6 sources,
+    1000 sweeps; p50/p99 latency and bins/s."""
+    from paper_1608_05179_gb300 import damas as D
+    from paper_1608_05179_gb300 import serve as SV
+    ctx = D.Context(0)
+    specs = synth.serve_requests(seed=5, n=args.requests)
+    reqs = []
+    for sp in specs:
+        rng = np.random.default_rng(sp["seed"])
+        freqs = np.sort(rng.uniform(sp["f_lo"], sp["f_hi"], sp["n_bins"]))
+        scn = synth.scene_random(rng, sp["M"], sp["N"], sp["n_src"], float(freqs[0]))
+        Cs = np.stack([synth.simulate_csm(scn.mics, scn.src_xyz, scn.powers, f, scn.c, 20.0, rng) for f in freqs])
+        L = {41: 3, 81: 4, 121: 3, 161: 5}[sp["N"]]
+        reqs.append(SV.Request(scn.mics, scn.grid, freqs, Cs, iters=1000, levels=L, eps=sp["keep_frac"]))
+    srv = SV.Server(ctx, max_inflight=8)
+    t0 = time.perf_counter()
+    tickets = []
+    for sp, r in zip(specs, reqs):
+        while time.perf_counter() - t0 < sp["t_arrive"]:
+            time.sleep(1e-4)
+        tickets.append(srv.submit(r))
+    res = [srv.wait(t, timeout=600) for t in tickets]
+    srv.stop()
+    lat = np.array([r.latency for r in res]) * 1e3
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    bins = sum(len(r.total_power) for r in res)
+    ctx.close()
+    return {"metric": "serving latency and throughput", "workload": f"{len(res)} requests, Poisson 200 req/s, 1000 sweeps",
+            "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "bins": bins, "bins_per_s": round(bins / span, 2), "span_s": round(span, 2)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,7 +441,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="spiral81", choices=["spiral81", "band", "large", "serve"],
+                    help="spiral81 is the benchmark line; the others print their own figures")
+    ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = 1024)")
+    ap.add_argument("--requests", type=int, default=32, help="serve: number of requests")
     args = ap.parse_args()
+    if args.workload != "spiral81":
+        from paper_1608_05179_gb300 import build as B
+        B.build()
+        fn = {"band": run_band, "large": run_large, "serve": run_serve}[args.workload]
+        print(json.dumps(fn(args)))
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
