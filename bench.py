@@ -255,13 +255,13 @@ def run_gpu(args, rank, world, local_rank):
                       "speedup_compressed_vs_full": round(value / full_bins, 2)},
         "roofline": {"kernel": "damas_sweep_kernel (compressed grid)", "bound": "hbm", "achieved": round(ach_c, 1),
                      "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_c / hbm_peak, 4),
-                     "traffic": traffic.get("compressed"), "peak_kind": peak_kind,
+                     "traffic": traffic.get("sweep_spiral81_compressed"), "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_c, "launch_ms": round(sweep_c_ms, 4),
                      "note": "A (S~ x S~ FP32, 1.7 MB) is read once per sweep in the algorithm; the kernel keeps it "
                              "in shared memory, so the launch is bound by the sequential row chain, not HBM"},
         "roofline_full_grid": {"kernel": "damas_sweep_kernel (full grid)", "bound": "hbm", "achieved": round(ach_f, 1),
                                "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_f / hbm_peak, 4),
-                               "traffic": traffic.get("full"), "algorithmic_bytes_per_launch": bytes_f,
+                               "traffic": traffic.get("sweep_spiral81_full"), "algorithmic_bytes_per_launch": bytes_f,
                                "launch_ms": round(sweep_f_ms, 3)},
         "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
@@ -273,13 +273,21 @@ def run_gpu(args, rank, world, local_rank):
 
 
 def _traffic_from_profiles():
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(p):
-        try:
-            return json.load(open(p))
-        except ValueError:
-            return {}
-    return {}
+    """DRAM bytes per launch from profiles/traffic.txt, only for kernels whose source is unchanged."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    if not os.path.exists(p):
+        return out
+    for line in open(p):
+        f = line.split()
+        if not f or f[0].startswith("#") or len(f) != 4:
+            continue
+        key, nbytes, src, sha = f
+        path = os.path.join(ROOT, "paper_1608_05179_gb300", src)
+        if os.path.exists(path) and hashlib.sha256(open(path, "rb").read()).hexdigest() == sha:
+            out[key] = int(nbytes)
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)
