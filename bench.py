@@ -408,6 +408,45 @@ def run_large(args):
     return out
 
 
+def run_psf(args):
+    """PSF matrix build (steering vectors, TF32 split, tensor-core Gram) for three
+    formulation-E grids; 2 warm-up and 5 timed builds each, in this order."""
+    import torch
+    from paper_1608_05179_gb300 import damas as D
+    ctx = D.Context(0)
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak_tf = float(json.load(open(pk))["bf16_tflops"]) if os.path.exists(pk) else 1900.0
+    tf32_peak = peak_tf / 2.0   # nominal dense TF32 rate is half the BF16 rate
+    cases = [("81x81 spiral, M=64", synth.scene_spiral_81()), ("121x121 spiral, M=64", synth.scene_band_121(n_bins=1)[0]),
+             ("161x161 spiral, M=128", synth.scene_large_161())]
+    res = []
+    for name, sc in cases:
+        geom = D.Geometry.from_scene(sc.mics, sc.grid, sc.c)
+        freq = float(sc.freq)
+        A, g2 = D.damas_build_psf(ctx, geom, freq)
+        D.damas_build_psf(ctx, geom, freq, A=A, gnorm2=g2)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            D.damas_build_psf(ctx, geom, freq, A=A, gnorm2=g2)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        S, M = sc.grid.S, sc.M
+        ms = statistics.median(ts)
+        mpad = -(-M // 16) * 16
+        tensor_flops = 3 * 8.0 * mpad * S * S / 2      # 3 TF32 products per FP32 product, symmetric half
+        res.append({"case": name, "S": S, "M": M, "ms": round(ms, 3),
+                    "tf32_tflops": round(tensor_flops / (ms / 1e3) / 1e12, 1),
+                    "tf32_frac_of_peak": round(tensor_flops / (ms / 1e3) / 1e12 / tf32_peak, 3),
+                    "write_gbs": round(float(S) * D.damas_lda(S) * 4 / (ms / 1e3) / 1e9, 1)})
+        del A
+    ctx.close()
+    return {"metric": "PSF build (steer + split + tcgen05 3xTF32 Gram), FP32 A", "tf32_peak_tflops": tf32_peak,
+            "peak_kind": "half of the measured BF16 burst rate" if os.path.exists(pk) else "fallback", "cases": res}
+
+
 def run_serve(args):
     """Poisson stream (200 req/s) of independent requests: M in {32,64,128}, grid side
     in {41,81,121,161}, 1-32 bins in 1-10 kHz, kept fraction 2-30%, 1-6 sources,
@@ -449,7 +488,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="spiral81", choices=["spiral81", "band", "large", "serve"],
+    ap.add_argument("--workload", default="spiral81", choices=["spiral81", "band", "large", "serve", "psf"],
                     help="spiral81 is the benchmark line; the others print their own figures")
     ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = 1024)")
     ap.add_argument("--requests", type=int, default=32, help="serve: number of requests")
@@ -457,7 +496,7 @@ def main():
     if args.workload != "spiral81":
         from paper_1608_05179_gb300 import build as B
         B.build()
-        fn = {"band": run_band, "large": run_large, "serve": run_serve}[args.workload]
+        fn = {"band": run_band, "large": run_large, "serve": run_serve, "psf": run_psf}[args.workload]
         print(json.dumps(fn(args)))
         return
     args.warmup = max(args.warmup, 3)

@@ -83,7 +83,7 @@ GeomK to_kernel(const damas_geom *g, double f) {
     return k;
 }
 
-inline int planes_ld(int M) { return round_up(M, 4); }
+inline int planes_ld(int M) { return round_up(M, 16); }  // whole 16-microphone chunks for the Gram
 
 }  // namespace
 
@@ -144,7 +144,8 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     const int ldm = planes_ld(geom->M);
     const int nplanes = geom->formulation == DAMAS_FORM_P ? 4 : 2;
     const size_t plane = (size_t)S_sub * ldm;
-    rc = ctx_ensure(ctx, ctx->planes, plane * nplanes * sizeof(float));
+    const size_t work = psf_work_floats(S_sub, ldm, nplanes == 2);
+    rc = ctx_ensure(ctx, ctx->planes, (plane * nplanes + work) * sizeof(float));
     if (rc) return rc;
     float *base = (float *)ctx->planes.ptr;
     float *Lre = base, *Lim = base + plane;
@@ -153,7 +154,8 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     const int kind = geom->formulation == DAMAS_FORM_P ? 2 : 0;
     DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, idx_dev, S_sub, Lre, Lim, Rre, Rim, ldm, gnorm2_dev, st));
     const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
-    DAMAS_CUDA_TRY(ctx, launch_psf_gram(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, a_dtype, st));
+    DAMAS_CUDA_TRY(ctx, launch_psf_gram(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, a_dtype,
+                                        base + plane * nplanes, st));
     return DAMAS_OK;
 }
 

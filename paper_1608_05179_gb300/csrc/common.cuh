@@ -59,9 +59,12 @@ struct GeomK {
 // (formulation P).  gnorm2 (optional) receives ||g||^2.
 cudaError_t launch_steer(const GeomK &g, int kind, const int32_t *idx, int n, float *Lre, float *Lim, float *Rre,
                          float *Rim, int ldm, float *gnorm2, cudaStream_t st);
-// A[n][s] = scale * |sum_m conj(L_nm) R_sm|^2 with unit diagonal, zero padding to lda.
+// A[n][s] = scale * |sum_m conj(L_nm) R_sm|^2 with unit diagonal, zero padding to
+// lda, on the tensor cores (tcgen05, 3xTF32); ldm must be a multiple of 16 and
+// work must hold psf_work_floats() floats of device scratch.
 cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm,
-                            int M, int S, float scale, void *A, int lda, int a_dtype, cudaStream_t st);
+                            int M, int S, float scale, void *A, int lda, int a_dtype, float *work, cudaStream_t st);
+size_t psf_work_floats(int S, int ldm, bool symmetric);
 // b_n = scale * Re(L_n^H C L_n) for n < S.
 cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,
                        float *b, cudaStream_t st);

@@ -86,6 +86,50 @@ def test_psf_selected_points_and_bf16(ctx):
     assert np.allclose(g2.cpu().numpy(), g2o, rtol=1e-6)
 
 
+def gram_tolerance(M):
+    """Bound on max |A_gpu - A| (entries in [0, 1]) for the 3xTF32 tensor-core Gram.
+
+    Every partial sum of G = e_n^H e_m has modulus <= 1 (Cauchy-Schwarz on unit
+    vectors; the same after the 1/M scaling of formulation P); each of the
+    12 * ceil(M / 16) MMA accumulations into Re G or Im G loses at most one FP32
+    ulp of such a value (2^-23, the accumulator truncates); the dropped lo*lo
+    products and the rounding of the lo parts add at most 2^-21; A = |G|^2
+    doubles the error of |G|; 1e-6 covers the FP32 vectors themselves."""
+    return 2.0 * (12 * math.ceil(M / 16) * 2.0 ** -23 + 2.0 ** -21) + 1e-6
+
+
+@pytest.mark.parametrize("M", [128, 256])
+@pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
+def test_psf_large_arrays(ctx, M, form):
+    mics = synth.mic_log_spiral(M, 8, 1.5)
+    grid = synth.square_plane(21, 2.0, 1.5)
+    g = D.Geometry.from_scene(mics, grid, synth.SPEED_OF_SOUND, form)
+    A, _ = D.damas_build_psf(ctx, g, 3000.0)
+    torch.cuda.synchronize()
+    Ao, _ = O.psf_matrix(mics, grid.points(), 3000.0, synth.SPEED_OF_SOUND, form)
+    Ag = A.cpu().numpy()[:, :grid.S]
+    assert np.abs(Ag - Ao).max() <= gram_tolerance(M)
+    assert np.all(np.diag(Ag) == 1.0)
+    if form == O.FORM_E:
+        assert np.array_equal(Ag, Ag.T)
+
+
+def test_psf_tiles_ragged_and_tiny(ctx):
+    """Sizes around the 128 x 256 tile edges and a single point."""
+    sc = synth.scene_spiral_81()
+    g = geom_of(sc)
+    pts = sc.grid.points()
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 127, 128, 129, 255, 256, 257, 300, 513):
+        idx = np.sort(rng.choice(sc.grid.S, n, replace=False)).astype(np.int32)
+        A, _ = D.damas_build_psf(ctx, g, sc.freq, torch.as_tensor(idx, device="cuda"), n)
+        torch.cuda.synchronize()
+        Ao, _ = O.psf_matrix(sc.mics, pts[idx], sc.freq, sc.c)
+        Ag = A.cpu().numpy()
+        assert np.abs(Ag[:, :n] - Ao).max() <= 5e-6, n
+        assert np.all(Ag[:, n:] == 0.0) and np.array_equal(Ag[:, :n], Ag[:, :n].T), n
+
+
 # ----------------------------------------------------------------------------- a2
 @pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
 @pytest.mark.parametrize("which", ["small", "spiral"])
