@@ -284,6 +284,133 @@ __device__ __forceinline__ float solve_block(const Team &T, const uint32_t *As, 
     return __fsub_rn(x_new, x_old);
 }
 
+// One warp: for the rows of own block Jb, bnd = sum over j < k of A_kj x_j with
+// the block's current x.  x of a block changes only when the block is solved,
+// so a bound computed after one solve serves the next one, off the critical
+// path (see solve_block2).
+template <bool F32, bool RES>
+__device__ __forceinline__ void block_bound(const SweepSys &s, const Team &T, const uint32_t *As, int Jb,
+                                            const float *xs, float *bnd) {
+    const int k = threadIdx.x & 31;
+    const int r = Jb * 32 - T.row0 + k;
+    const bool valid = Jb * 32 + k < T.S;
+    const float xk = valid ? xs[r] : 0.f;
+    unsigned m = __ballot_sync(FULL, xk > 0.f);
+    float b = 0.f;
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        const float xj = __shfl_sync(FULL, xk, j);
+        if (valid && j < k) {
+            const float a = RES ? res_at<F32>(T, As, r, Jb * 32 + j) : col_at<F32>(s, Jb * 32 + j, T.row0 + r);
+            b = __fmaf_rn(a, xj, b);
+        }
+    }
+    if (valid) bnd[r] = b;
+}
+
+// Warp 0 solves own block J, as solve_block, with the bound of each row taken
+// from bnd (block_bound) instead of computed here.  The chain takes the
+// candidate rows eight at a time: their positions are pulled from the mask and
+// their eight coefficients loaded together before the dependent steps run.
+template <bool F32, bool RES>
+__device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As, const char *tiles, int J, int Jm1,
+                                              float *xs, const float *rh, const float *rl, const float *bnd,
+                                              const float *dm1, bool nonneg) {
+    const int k = threadIdx.x & 31;
+    const int i = J * 32 + k, r = i - T.row0;
+    const bool valid = i < T.S;
+    const char *tdiag = tiles, *tpart = tiles + 32 * T.tile_ld;
+    auto diag_at = [&](int j) -> float {
+        return RES ? (valid ? res_at<F32>(T, As, r, J * 32 + j) : 0.f) : tile_at<F32>(T, tdiag, j, k);
+    };
+    auto part_at = [&](int c) -> float {
+        return RES ? (valid ? res_at<F32>(T, As, r, Jm1 * 32 + c) : 0.f) : tile_at<F32>(T, tpart, c, k);
+    };
+    const float x_old = valid ? xs[r] : 0.f;
+    float w = valid ? -__fadd_rn(rh[r], rl[r]) : 0.f;
+    const float bound = valid ? bnd[r] : 0.f;
+
+    // dx of the previous step on this block's rows
+    const unsigned m1 = dm1 ? __ballot_sync(FULL, dm1[k] != 0.f) : 0u;
+    if (__popc(m1) > 6) {
+        float a[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) a[c] = part_at(c);
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+            p0 = __fmaf_rn(a[c], dm1[c], p0);
+            p1 = __fmaf_rn(a[c + 1], dm1[c + 1], p1);
+            p2 = __fmaf_rn(a[c + 2], dm1[c + 2], p2);
+            p3 = __fmaf_rn(a[c + 3], dm1[c + 3], p3);
+        }
+        w = __fsub_rn(w, __fadd_rn(__fadd_rn(p0, p1), __fadd_rn(p2, p3)));
+    } else if (m1) {
+        float p0 = 0.f;
+        unsigned m = m1;
+        while (m) {
+            const int c = __ffs(m) - 1;
+            m &= m - 1u;
+            p0 = __fmaf_rn(part_at(c), dm1[c], p0);
+        }
+        w = __fsub_rn(w, p0);
+    }
+
+    // which rows can move: x > 0, or w + (the most the block's earlier rows can
+    // raise w) > 0
+    unsigned mask;
+    if (nonneg) {
+        const float margin = 3.8e-6f * (fabsf(w) + bound);
+        mask = __ballot_sync(FULL, valid && (x_old > 0.f || __fadd_rn(w, bound) > -margin));
+    } else {
+        mask = __ballot_sync(FULL, valid);
+    }
+
+    const float xneg = -x_old;
+    float dchain = 0.f;
+    if (__popc(mask) > 16) {
+        float arow[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) arow[j] = diag_at(j);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float wj = __shfl_sync(FULL, w, j);
+            const float d = fmaxf(wj, __shfl_sync(FULL, xneg, j));
+            w = __fmaf_rn(-arow[j], d, w);
+            if (k == j) dchain = d;
+        }
+    } else {
+        unsigned m = mask;
+        while (m) {
+            int c[8], cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = m ? __ffs(m) - 1 : 0;
+                if (m) {
+                    m &= m - 1u;
+                    ++cnt;
+                }
+            }
+            float a[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = diag_at(c[q]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= cnt) break;
+                const int j = c[q];
+                const float wj = __shfl_sync(FULL, w, j);
+                const float d = fmaxf(wj, __shfl_sync(FULL, xneg, j));
+                w = __fmaf_rn(-a[q], d, w);
+                if (k == j) dchain = d;
+            }
+        }
+    }
+    const float x_new = __fadd_rn(x_old, dchain);  // = max(x - r, 0)
+    if (valid) xs[r] = x_new;
+    return __fsub_rn(x_new, x_old);
+}
+
 template <bool F32, bool RES>
 __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &s, float (*dring)[32],
                                           unsigned char (*nzidx)[32], int *nzcnt, int *s_abort_p, char *smem) {
@@ -308,8 +435,9 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
     float *rh = (float *)smem;
     float *rl = rh + T.R;
     float *xs = rl + T.R;
-    uint32_t *As = (uint32_t *)(xs + T.R);  // resident rows of A
-    char *tiles = (char *)(xs + T.R);       // or: two slots of two chain tiles
+    float *bnd = xs + T.R;                   // per-row bound for candidate detection
+    uint32_t *As = (uint32_t *)(bnd + T.R);  // resident rows of A
+    char *tiles = (char *)(bnd + T.R);       // or: two slots of two chain tiles
     const int slot_bytes = 2 * 32 * T.tile_ld;
 
     // ---- prologue
@@ -385,6 +513,8 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
         }
         nonneg_all = !__syncthreads_or(negs);
     }
+    if (pipelined)
+        for (int Jb = T.jb0 + warp; Jb < T.jb1; Jb += SW_THREADS / 32) block_bound<F32, RES>(s, T, As, Jb, xs, bnd);
     if (warp == 0 && tile_blk0 >= 0) cp_async_wait_all();
     __syncthreads();
 
@@ -426,7 +556,8 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
                     cp_async_wait_all();
                     __syncwarp();
                 }
-                const float dk = solve_block<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, dring[g1], nonneg_all);
+                const float dk =
+                    solve_block2<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, bnd, dring[g1], nonneg_all);
                 if (J != p.withhold_block)
                     st_relaxed_u64(s.mbox + (size_t)J * 32 + lane,
                                    ((unsigned long long)epoch << 32) | __float_as_uint(dk));
@@ -493,6 +624,9 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
                     }
                 }
             }
+            // block J-1 was solved in the previous step: its bound for the next sweep
+            if (ownJm1 && Jm1 != J && upd_index(warp) == ((Jm1 * 32 - T.row0) >> 5) % UPD_WARPS)
+                block_bound<F32, RES>(s, T, As, Jm1, xs, bnd);
         }
         __syncthreads();
         if (s_abort) {
@@ -547,7 +681,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepP
 
 size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident) {
     const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
-    size_t b = (size_t)3 * R * sizeof(float);
+    size_t b = (size_t)4 * R * sizeof(float);
     if (resident)
         b += (size_t)R * ((size_t)lda * elt / 4 + 1) * 4;
     else
