@@ -298,31 +298,49 @@ __device__ __forceinline__ void block_bound(const SweepSys &s, const Team &T, co
     unsigned m = __ballot_sync(FULL, xk > 0.f);
     float b = 0.f;
     while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1u;
-        const float xj = __shfl_sync(FULL, xk, j);
-        if (valid && j < k) {
-            const float a = RES ? res_at<F32>(T, As, r, Jb * 32 + j) : col_at<F32>(s, Jb * 32 + j, T.row0 + r);
-            b = __fmaf_rn(a, xj, b);
+        int c[8], cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            c[q] = m ? __ffs(m) - 1 : 0;
+            if (m) {
+                m &= m - 1u;
+                ++cnt;
+            }
         }
+        float a[8], xj[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            xj[q] = __shfl_sync(FULL, xk, c[q]);
+            a[q] = !valid || q >= cnt ? 0.f
+                   : RES                  ? res_at<F32>(T, As, r, Jb * 32 + c[q])
+                                          : col_at<F32>(s, Jb * 32 + c[q], T.row0 + r);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < cnt && c[q] < k) b = __fmaf_rn(a[q], xj[q], b);
     }
     if (valid) bnd[r] = b;
 }
 
-// Warp 0 solves own block J, as solve_block, with the bound of each row taken
-// from bnd (block_bound) instead of computed here.  The chain takes the
-// candidate rows eight at a time: their positions are pulled from the mask and
-// their eight coefficients loaded together before the dependent steps run.
+// Warp 0 solves own block J: the same arithmetic as solve_block, arranged for
+// latency.  The bound of each row comes from bnd (block_bound); dx of the
+// previous step arrives in a register (dprev: this lane's entry) and is
+// broadcast by shuffles.  The chain takes the candidate rows eight at a time:
+// their positions are pulled from the mask and their coefficients loaded
+// together before the dependent steps run (a dense pass over all 32 rows when
+// more than 16 can move).
 template <bool F32, bool RES>
 __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As, const char *tiles, int J, int Jm1,
                                               float *xs, const float *rh, const float *rl, const float *bnd,
-                                              const float *dm1, bool nonneg) {
+                                              float dprev, bool have_prev, bool nonneg) {
     const int k = threadIdx.x & 31;
     const int i = J * 32 + k, r = i - T.row0;
     const bool valid = i < T.S;
     const char *tdiag = tiles, *tpart = tiles + 32 * T.tile_ld;
-    auto diag_at = [&](int j) -> float {
-        return RES ? (valid ? res_at<F32>(T, As, r, J * 32 + j) : 0.f) : tile_at<F32>(T, tdiag, j, k);
+    // A[32J + row][32J + col] and A[32J + row][32 Jm1 + col], rows and columns within the blocks
+    auto diag_rc = [&](int row, int col) -> float {
+        return RES ? (J * 32 + row < T.S ? res_at<F32>(T, As, J * 32 + row - T.row0, J * 32 + col) : 0.f)
+                   : tile_at<F32>(T, tdiag, col, row);
     };
     auto part_at = [&](int c) -> float {
         return RES ? (valid ? res_at<F32>(T, As, r, Jm1 * 32 + c) : 0.f) : tile_at<F32>(T, tpart, c, k);
@@ -332,7 +350,7 @@ __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As,
     const float bound = valid ? bnd[r] : 0.f;
 
     // dx of the previous step on this block's rows
-    const unsigned m1 = dm1 ? __ballot_sync(FULL, dm1[k] != 0.f) : 0u;
+    const unsigned m1 = have_prev ? __ballot_sync(FULL, dprev != 0.f) : 0u;
     if (__popc(m1) > 6) {
         float a[32];
 #pragma unroll
@@ -340,19 +358,34 @@ __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As,
         float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
         for (int c = 0; c < 32; c += 4) {
-            p0 = __fmaf_rn(a[c], dm1[c], p0);
-            p1 = __fmaf_rn(a[c + 1], dm1[c + 1], p1);
-            p2 = __fmaf_rn(a[c + 2], dm1[c + 2], p2);
-            p3 = __fmaf_rn(a[c + 3], dm1[c + 3], p3);
+            p0 = __fmaf_rn(a[c], __shfl_sync(FULL, dprev, c), p0);
+            p1 = __fmaf_rn(a[c + 1], __shfl_sync(FULL, dprev, c + 1), p1);
+            p2 = __fmaf_rn(a[c + 2], __shfl_sync(FULL, dprev, c + 2), p2);
+            p3 = __fmaf_rn(a[c + 3], __shfl_sync(FULL, dprev, c + 3), p3);
         }
         w = __fsub_rn(w, __fadd_rn(__fadd_rn(p0, p1), __fadd_rn(p2, p3)));
     } else if (m1) {
         float p0 = 0.f;
         unsigned m = m1;
         while (m) {
-            const int c = __ffs(m) - 1;
-            m &= m - 1u;
-            p0 = __fmaf_rn(part_at(c), dm1[c], p0);
+            int c[6], cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                c[q] = m ? __ffs(m) - 1 : 0;
+                if (m) {
+                    m &= m - 1u;
+                    ++cnt;
+                }
+            }
+            float a[6], dd[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                a[q] = part_at(c[q]);
+                dd[q] = __shfl_sync(FULL, dprev, c[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                if (q < cnt) p0 = __fmaf_rn(a[q], dd[q], p0);
         }
         w = __fsub_rn(w, p0);
     }
@@ -372,7 +405,7 @@ __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As,
     if (__popc(mask) > 16) {
         float arow[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) arow[j] = diag_at(j);
+        for (int j = 0; j < 32; ++j) arow[j] = diag_rc(k, j);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             const float wj = __shfl_sync(FULL, w, j);
@@ -394,7 +427,7 @@ __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As,
             }
             float a[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = diag_at(c[q]);
+            for (int q = 0; q < 8; ++q) a[q] = diag_rc(k, c[q]);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (q >= cnt) break;
@@ -519,6 +552,7 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
     __syncthreads();
 
     // ---- steps
+    float dprev = dring[3][lane];  // warp 0: this lane's dx of the previous step
     int J = 0;
     unsigned epoch = s.epoch0 + 1u;
     for (long long G = 0; G < Gend; ++G) {
@@ -557,7 +591,8 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
                     __syncwarp();
                 }
                 const float dk =
-                    solve_block2<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, bnd, dring[g1], nonneg_all);
+                    solve_block2<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, bnd, dprev, true, nonneg_all);
+                dprev = dk;
                 if (J != p.withhold_block)
                     st_relaxed_u64(s.mbox + (size_t)J * 32 + lane,
                                    ((unsigned long long)epoch << 32) | __float_as_uint(dk));
@@ -601,6 +636,7 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
                     }
                 }
                 const float d = __uint_as_float((unsigned)w);
+                dprev = d;
                 dring[gi][lane] = d;
                 make_list(d, nzidx[gi], &nzcnt[gi]);
             }
