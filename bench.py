@@ -447,21 +447,14 @@ def run_psf(args):
             "peak_kind": "half of the measured BF16 burst rate" if os.path.exists(pk) else "fallback", "cases": res}
 
 
-def run_serve(args):
-    """Poisson stream (200 req/s) of independent requests: M in {32,64,128}, grid side
-    in {41,81,121,161}, 1-32 bins in 1-10 kHz, kept fraction 2-30%, 1-6 sources,
-    1000 sweeps; p50/p99 latency and bins/s."""
-    from paper_1608_05179_gb300 import damas as D
-    from paper_1608_05179_gb300 import serve as SV
-    ctx = D.Context(0)
-    specs = synth.serve_requests(seed=5, n=args.requests)
+def _serve_stream(D, SV, ctx, specs, full: bool):
     reqs = []
     for sp in specs:
         rng = np.random.default_rng(sp["seed"])
         freqs = np.sort(rng.uniform(sp["f_lo"], sp["f_hi"], sp["n_bins"]))
         scn = synth.scene_random(rng, sp["M"], sp["N"], sp["n_src"], float(freqs[0]))
         Cs = np.stack([synth.simulate_csm(scn.mics, scn.src_xyz, scn.powers, f, scn.c, 20.0, rng) for f in freqs])
-        L = {41: 3, 81: 4, 121: 3, 161: 5}[sp["N"]]
+        L = 0 if full else {41: 3, 81: 4, 121: 3, 161: 5}[sp["N"]]
         reqs.append(SV.Request(scn.mics, scn.grid, freqs, Cs, iters=1000, levels=L, eps=sp["keep_frac"]))
     srv = SV.Server(ctx, max_inflight=8)
     t0 = time.perf_counter()
@@ -470,15 +463,31 @@ def run_serve(args):
         while time.perf_counter() - t0 < sp["t_arrive"]:
             time.sleep(1e-4)
         tickets.append(srv.submit(r))
-    res = [srv.wait(t, timeout=600) for t in tickets]
+    res = [srv.wait(t, timeout=1800) for t in tickets]
     srv.stop()
     lat = np.array([r.latency for r in res]) * 1e3
     span = max(r.t_done for r in res) - min(r.t_submit for r in res)
     bins = sum(len(r.total_power) for r in res)
+    rows = int(sum(int(np.sum(r.S_sub)) for r in res))
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "bins": bins, "rows_solved": rows, "bins_per_s": round(bins / span, 2), "span_s": round(span, 2)}
+
+
+def run_serve(args):
+    """Poisson stream (200 req/s) of independent requests: M in {32,64,128}, grid side
+    in {41,81,121,161}, 1-32 bins in 1-10 kHz, kept fraction 2-30%, 1-6 sources,
+    1000 sweeps; p50/p99 latency and bins/s.  With --serve-full the same stream is
+    served again on the full grids (no compression) for comparison."""
+    from paper_1608_05179_gb300 import damas as D
+    from paper_1608_05179_gb300 import serve as SV
+    ctx = D.Context(0)
+    specs = synth.serve_requests(seed=5, n=args.requests)
+    out = {"metric": "serving latency and throughput", "workload": f"{len(specs)} requests, Poisson 200 req/s, "
+           "1000 sweeps", **_serve_stream(D, SV, ctx, specs, full=False)}
+    if args.serve_full:
+        out["full_grid"] = _serve_stream(D, SV, ctx, specs, full=True)
     ctx.close()
-    return {"metric": "serving latency and throughput", "workload": f"{len(res)} requests, Poisson 200 req/s, 1000 sweeps",
-            "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
-            "bins": bins, "bins_per_s": round(bins / span, 2), "span_s": round(span, 2)}
+    return out
 
 
 def main():
@@ -492,6 +501,7 @@ def main():
                     help="spiral81 is the benchmark line; the others print their own figures")
     ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = 1024)")
     ap.add_argument("--requests", type=int, default=32, help="serve: number of requests")
+    ap.add_argument("--serve-full", action="store_true", help="serve: also serve the stream on the full grids")
     args = ap.parse_args()
     if args.workload != "spiral81":
         from paper_1608_05179_gb300 import build as B
