@@ -107,6 +107,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- ranks
+def rank_seed(rank: int) -> int:
+    """Scene seed of a rank: every rank solves its own, independent bins."""
+    return 1 + rank
+
+
+def reduce_max(values, world: int, device):
+    """Element-wise max over ranks (the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -114,7 +135,7 @@ def run_gpu(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    sc = synth.scene_spiral_81(seed=1 + rank)
+    sc = synth.scene_spiral_81(seed=rank_seed(rank))
     ctx = D.Context(local_rank)
     geom = D.Geometry.from_scene(sc.mics, sc.grid, sc.c, device=dev)
     C_dev = D.csm_tensor(sc.C, device=dev)
@@ -222,17 +243,11 @@ def run_gpu(args, rank, world, local_rank):
     d2h = x_host.numel() * 4 + 8
 
     # max over ranks
-    tot_c = float(sum(c_ms))
-    tot_f = float(sum(f_ms))
-    tot_e = float(sum(e_ms))
-    if world > 1:
-        t = torch.tensor([tot_c, tot_f, tot_e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_c, tot_f, tot_e = t.tolist()
+    tot_c, tot_f, tot_e = reduce_max([sum(c_ms), sum(f_ms), sum(e_ms)], world, dev)
     ms_step = tot_c / args.steps
-    value = world * args.steps / (tot_c / 1e3)
-    full_bins = world * k_full / (tot_f / 1e3)
-    e2e_val = world * args.steps / (tot_e / 1e3)
+    value = job_throughput(args.steps, world, tot_c)
+    full_bins = job_throughput(k_full, world, tot_f)
+    e2e_val = job_throughput(args.steps, world, tot_e)
 
     hbm_peak, peak_kind = _peaks()
     lda_c = D.damas_lda(S_sub)

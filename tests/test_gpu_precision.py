@@ -57,6 +57,7 @@ def test_bf16_bulk_with_fp32_refinement_per_source_db(ctx):
     beam = 1.22 * 1.5 * sc.c / (1.5 * sc.freq)      # Rayleigh beamwidth at the plane (§5), z0 = D = 1.5 m
     ref = region_power_db(O.scatter(x_orc, idx, sc.grid.S), sc.grid, sc.src_xyz, beam / 2)
     err = {k: np.abs(region_power_db(v, sc.grid, sc.src_xyz, beam / 2) - ref) for k, v in runs.items()}
+    print("per-source |dB error| vs FP64 oracle:", {k: np.round(v, 3).tolist() for k, v in err.items()})
     assert err["fp32"].max() <= 0.05, err["fp32"]
     assert err["bf16+fp32"].max() <= 0.5, err["bf16+fp32"]
     assert err["bf16+fp32"].max() <= err["bf16"].max() + 1e-6
