@@ -97,6 +97,11 @@ const char *damas_last_error(const damas_ctx *ctx);
  * S rounded up to a multiple of 32 (every row 128-byte aligned for FP32). */
 int damas_lda(int S);
 
+/* Floats of the optional solver state of a system with S unknowns (damas_system.state_dev):
+ * the residual as an FP32 pair per row plus the two last blocks of dx not yet folded into
+ * every row.  Returns 0 for S < 1. */
+int damas_state_floats(int S);
+
 /* ------------------------------------------------------------------ a1 + a4: PSF matrix */
 
 /*
@@ -226,7 +231,7 @@ typedef struct {
     int S;              /* number of unknowns, >= 1 */
     const float *b_dev; /* device float[S] */
     float *x_dev;       /* device float[S], in/out */
-    float *state_dev;   /* optional device float[2*S + 64]: the iteration's internal state
+    float *state_dev;   /* optional device float[damas_state_floats(S)] (2*S + 64): the iteration's internal state
                            (residual as an FP32 pair hi/lo plus the last two blocks of
                            dx not yet folded into every row); opaque, written at the
                            end of every solve, read with DAMAS_INIT_STATE */

@@ -64,6 +64,7 @@ SIGNATURES = {
     "damas_destroy": (c_int, [c_void_p]),
     "damas_last_error": (ctypes.c_char_p, [c_void_p]),
     "damas_lda": (c_int, [c_int]),
+    "damas_state_floats": (c_int, [c_int]),
     "damas_build_psf": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_int, c_void_p,
                                 c_int, c_void_p, c_void_p]),
     "das_map": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_void_p, c_void_p]),

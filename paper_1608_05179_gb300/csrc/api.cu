@@ -126,6 +126,8 @@ const char *damas_last_error(const damas_ctx *ctx) { return ctx ? ctx->err : "no
 
 int damas_lda(int S) { return S <= 0 ? 0 : round_up(S, 32); }
 
+int damas_state_floats(int S) { return S <= 0 ? 0 : 2 * S + 64; }
+
 // ----------------------------------------------------------------------------- PSF matrix
 int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev, int S_sub,
                     int a_dtype, void *A_dev, int lda, float *gnorm2_dev, damas_stream stream) {

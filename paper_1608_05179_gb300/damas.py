@@ -106,6 +106,11 @@ def damas_lda(S: int) -> int:
     return _lib.load().damas_lda(int(S))
 
 
+def damas_state_floats(S: int) -> int:
+    """Length of the solver state of an S-unknown system (System.state)."""
+    return _lib.load().damas_state_floats(int(S))
+
+
 def damas_build_psf(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor | None = None, S_sub: int | None = None,
                     a_dtype: int = F32, A: torch.Tensor | None = None, gnorm2: torch.Tensor | None = None,
                     stream=None):

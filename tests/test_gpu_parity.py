@@ -33,10 +33,14 @@ def ctx():
 
 
 def rel_l2(a, b):
+    """Relative L2 error of a against b; the value is printed (pytest -s) so a run records it."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+    e = float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+    import inspect
+    print(f"[rel_l2] {inspect.stack()[1].function}: {e:.3e}")
+    return e
 
 
 def geom_of(sc, form=O.FORM_E):
@@ -253,6 +257,19 @@ def _compressed_system():
     return A, b[idx]
 
 
+@pytest.mark.slow
+def test_sweep_full_grid_81x81_1000_sweeps(ctx):
+    """The benchmark's full-grid solve (S = 6561, 1000 sweeps, the automatic
+    launch plan) against the FP64 oracle on the same FP32 inputs."""
+    sc = synth.scene_spiral_81()
+    pts = sc.grid.points()
+    A, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c)
+    b = O.das_map(sc.mics, pts, sc.freq, sc.c, sc.C)
+    x = _solve_gpu(ctx, A, b, 1000)
+    xo = _oracle_fp32_inputs(A, b, 1000)
+    assert rel_l2(x, xo) <= 1e-4
+
+
 @pytest.mark.parametrize("ctas", [0, 1, 3, 7])
 def test_sweep_small_full_grid(ctx, ctas):
     sc = synth.scene_monopole_small()
@@ -341,7 +358,7 @@ def test_sweep_resume_is_bit_exact_and_deterministic(ctx, ctas, place):
     A = padded(A64)
     b = torch.as_tensor(b64.astype(np.float32), device="cuda")
     x1 = torch.zeros(S, device="cuda")
-    st = torch.zeros(2 * S + 64, device="cuda")
+    st = torch.zeros(D.damas_state_floats(S), device="cuda")
     D.damas_solve(ctx, D.System(A, b, x1, 300, state=st), ctas_per_system=ctas, a_placement=place)
     D.damas_solve(ctx, D.System(A, b, x1, 200, state=st, init=D.INIT_STATE), ctas_per_system=2, a_placement=2)
     x2 = torch.zeros(S, device="cuda")
