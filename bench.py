@@ -402,6 +402,10 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- other workloads (opt-in)
+def bs_cap(bs, cap):
+    return cap if cap else "SM count"
+
+
 def run_band(args):
     """64 bins log-spaced 1-8 kHz on a 121x121 grid, each bin compressed (linear
     prediction, 3 levels, relative threshold 1e-3), 1000 sweeps, all bins in one
@@ -420,7 +424,11 @@ def run_band(args):
            "band: 64 bins 1-8 kHz, 121x121 grid, M=64 spiral, 5 sources, linear L=3 rel 1e-3, 1000 sweeps",
            "S_f_min": min(grids.S_f), "S_f_max": max(grids.S_f), "S_f_sum": sum(grids.S_f)}
     for name, dt, elt in (("f32", D.F32, 4), ("bf16", D.BF16, 2)):
-        bs = BD.BandSolver(ctx, geom, freqs, grids.S_f, 1000, dt, rows_per_cta=args.rows or 1024)
+        if args.rows:
+            (rows, cap), tune = (args.rows, None), None
+        else:
+            (rows, cap), tune = BD.autotune_rows(ctx, geom, freqs, grids, iters_probe=20, a_dtype=dt)
+        bs = BD.BandSolver(ctx, geom, freqs, grids.S_f, 1000, dt, rows_per_cta=rows, capacity=cap)
         bs.capture(grids)
         for _ in range(2):
             bs.replay()
@@ -442,7 +450,9 @@ def run_band(args):
         solve_ms = s0.elapsed_time(s1)
         bytes_ = sum(float(n) * n for n in grids.S_f) * elt * 1000
         out[name] = {"bins_per_s": round(64 / (ms / 1e3), 2), "ms_per_band": round(ms, 2), "solve_ms": round(solve_ms, 2),
-                     "sweep_gbs": round(bytes_ / (solve_ms / 1e3) / 1e9, 1), "ctas": sum(bs.ctas)}
+                     "sweep_gbs": round(bytes_ / (solve_ms / 1e3) / 1e9, 1), "ctas": sum(bs.ctas),
+                     "rows_per_cta": rows, "cta_capacity": bs_cap(bs, cap),
+                     "autotune_s_per_20_sweeps": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tune.items()} if tune else None}
     ctx.close()
     return out
 
@@ -572,7 +582,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="spiral81", choices=["spiral81", "band", "large", "serve", "psf"],
                     help="spiral81 is the benchmark line; the others print their own figures")
-    ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = 1024)")
+    ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = chosen by the autotuner)")
     ap.add_argument("--requests", type=int, default=32, help="serve: number of requests")
     ap.add_argument("--serve-full", action="store_true", help="serve: also serve the stream on the full grids")
     args = ap.parse_args()

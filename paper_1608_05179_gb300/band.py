@@ -116,21 +116,30 @@ class BandSolver:
 
 
 def autotune_rows(ctx, geom, freqs, grids: BandGrids, iters_probe: int = 20, a_dtype: int = D.F32,
-                  candidates=(256, 512, 1024, 2048, 4096)):
-    """Pick rows per CTA for this band by timing a short solve of each candidate plan."""
+                  candidates=(256, 512, 1024, 2048), cta_per_sm=(1, 2)):
+    """Pick the team plan for this band - rows per CTA, and how many CTAs the
+    device is asked to hold at once (one or two per SM) - by timing a short solve
+    of each candidate.  Returns ((rows, capacity), {(rows, capacity): seconds})."""
+    sms = torch.cuda.get_device_properties(geom.mic_xyz.device).multi_processor_count
     best, timings = None, {}
-    for rows in candidates:
-        bs = BandSolver(ctx, geom, freqs, grids.S_f, iters_probe, a_dtype, rows)
-        bs.run(grids)
-        bs.check()
-        systems = bs.systems()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        D.damas_solve(ctx, systems, status=bs.status)
-        bs.check()
-        timings[rows] = time.perf_counter() - t0
-        if best is None or timings[rows] < timings[best]:
-            best = rows
+    for per_sm in cta_per_sm:
+        for rows in candidates:
+            cap = per_sm * sms
+            bs = BandSolver(ctx, geom, freqs, grids.S_f, iters_probe, a_dtype, rows, capacity=cap)
+            bs.run(grids)
+            bs.check()
+            systems = bs.systems()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                D.damas_solve(ctx, systems, status=bs.status)
+                bs.check()
+            except D.DamasError:
+                continue  # this plan does not fit the device at once
+            key = (rows, cap)
+            timings[key] = time.perf_counter() - t0
+            if best is None or timings[key] < timings[best]:
+                best = key
     return best, timings
 
 

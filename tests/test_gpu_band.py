@@ -94,4 +94,11 @@ def test_autotuner_picks_a_candidate(ctx):
     grids = B.compress_band(ctx, geom, freqs, C, 4, D.PRED_LINEAR, D.EPS_REL_MAX, 2e-3)
     grids.S_f = [int(v) for v in grids.S_f_dev.cpu().tolist()]
     best, timings = B.autotune_rows(ctx, geom, freqs, grids, iters_probe=5, candidates=(256, 1024))
-    assert best in (256, 1024) and set(timings) == {256, 1024}
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert best in timings and min(timings, key=timings.get) == best
+    assert {rows for rows, _ in timings} <= {256, 1024} and {cap for _, cap in timings} <= {sms, 2 * sms}
+    assert (256, sms) in timings and (1024, sms) in timings
+    # the chosen plan solves the band like any other
+    bs = B.BandSolver(ctx, geom, freqs, grids.S_f, 30, D.F32, best[0], capacity=best[1])
+    bs.run(grids)
+    bs.check()
