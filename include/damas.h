@@ -290,8 +290,8 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
 typedef struct {
     size_t hbm_budget_bytes; /* device memory the loop may hold for requests; 0 = half the free memory */
     int max_inflight;        /* requests on the device at once; 0 = 8 */
-    int sm_slots;            /* CTAs that concurrent solves may hold together; 0 = the SM count */
-    int rows_per_cta;        /* solver team size target, rows per CTA; 0 = 1024 */
+    int sm_slots;            /* CTAs that concurrent solves may hold together; 0 = twice the SM count */
+    int rows_per_cta;        /* solver team size target, rows per CTA; 0 = 512 */
 } damas_serve_cfg;
 
 typedef struct {

@@ -45,7 +45,7 @@ class Server:
     """damas_serve_start/submit/poll/release/stop on a context."""
 
     def __init__(self, ctx: Context, hbm_budget_bytes: int = 0, max_inflight: int = 8, sm_slots: int = 0,
-                 rows_per_cta: int = 1024):
+                 rows_per_cta: int = 0):
         self.ctx = ctx
         cfg = _lib.damas_serve_cfg(int(hbm_budget_bytes), int(max_inflight), int(sm_slots), int(rows_per_cta))
         ctx.check(ctx.lib.damas_serve_start(ctx.handle, ctypes.byref(cfg)))
