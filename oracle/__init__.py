@@ -52,11 +52,13 @@ def _load():
         lib.orc_vectors.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, dp, dp, dp]
         lib.orc_psf.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp, ctypes.c_int]
         lib.orc_das.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp]
+        lib.orc_das_dr.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp]
+        lib.orc_psf_dr.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp, ctypes.c_int]
         lib.orc_gauss_seidel.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp, ctypes.c_int]
         lib.orc_wavelet_select.argtypes = [ctypes.c_int, ctypes.c_int, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ip, fp, bp, fp]
         lib.orc_wavelet_select.restype = ctypes.c_int
-        for f in (lib.orc_vectors, lib.orc_psf, lib.orc_das, lib.orc_gauss_seidel):
+        for f in (lib.orc_vectors, lib.orc_psf, lib.orc_das, lib.orc_gauss_seidel, lib.orc_das_dr, lib.orc_psf_dr):
             f.restype = None
         _lib = lib
     return _lib
@@ -90,8 +92,10 @@ def vectors(mics, pts, freq, c, kind: str):
     return re + 1j * im, g2
 
 
-def psf_matrix(mics, pts, freq, c, form: int = FORM_E):
-    """A (S x S, FP64) of Eq. (10)/(12) with unit diagonal; also ||g_n||^2."""
+def psf_matrix(mics, pts, freq, c, form: int = FORM_E, diag_removal: bool = False):
+    """A (S x S, FP64) of Eq. (10)/(12) with unit diagonal; also ||g_n||^2.
+    diag_removal: the PSF without the m = m' microphone pairs (orc_psf_dr); its
+    diagonal is then computed, not 1."""
     lib = _load()
     M = np.asarray(mics).shape[0]
     if form == FORM_E:
@@ -105,12 +109,15 @@ def psf_matrix(mics, pts, freq, c, form: int = FORM_E):
     A = np.empty((S, S))
     lre, lim = _c64(L.real), _c64(L.imag)
     rre, rim = _c64(R.real), _c64(R.imag)
-    lib.orc_psf(S, M, _d(lre), _d(lim), _d(rre), _d(rim), scale, _d(A), S)
+    if diag_removal:
+        lib.orc_psf_dr(S, M, _d(lre), _d(lim), _d(rre), _d(rim), scale, _d(A), S)
+    else:
+        lib.orc_psf(S, M, _d(lre), _d(lim), _d(rre), _d(rim), scale, _d(A), S)
     return A, g2
 
 
-def das_map(mics, pts, freq, c, C, form: int = FORM_E, return_imag: bool = False):
-    """DAS map b of Eq. (2) (FP64)."""
+def das_map(mics, pts, freq, c, C, form: int = FORM_E, return_imag: bool = False, diag_removal: bool = False):
+    """DAS map b of Eq. (2) (FP64); diag_removal: without the CSM diagonal (orc_das_dr)."""
     lib = _load()
     M = np.asarray(mics).shape[0]
     if form == FORM_E:
@@ -126,7 +133,11 @@ def das_map(mics, pts, freq, c, C, form: int = FORM_E, return_imag: bool = False
     b = np.empty(S)
     bi = np.empty(S)
     lre, lim = _c64(L.real), _c64(L.imag)
-    lib.orc_das(S, M, _d(lre), _d(lim), _d(Ci), scale, _d(b), _d(bi))
+    if diag_removal:
+        lib.orc_das_dr(S, M, _d(lre), _d(lim), _d(Ci), scale, _d(b))
+        bi[:] = 0.0
+    else:
+        lib.orc_das(S, M, _d(lre), _d(lim), _d(Ci), scale, _d(b), _d(bi))
     return (b, bi) if return_imag else b
 
 

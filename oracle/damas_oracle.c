@@ -123,6 +123,58 @@ void orc_das(int S, int M, const double *re, const double *im, const double *C, 
 }
 
 /*
+ * Diagonal removal (§2: the auto-spectra on the CSM diagonal are dropped to
+ * suppress uncorrelated microphone self-noise).  Both the map and the PSF then
+ * exclude the m = m' terms of their double sums over microphone pairs:
+ *   b_n  = scale * Re( sum_{p != q} conj(l_np) C_pq l_nq )
+ *   A_ns = scale * sum_{m != m'} conj(l_nm) r_sm conj(r_sm') l_nm'
+ * (the PSF is the map of a unit source at s, C = r_s r_s^H).  A_nn is no
+ * longer 1; it is computed like every other entry.  Written as the plain
+ * double sums: O(M^2) per entry.
+ */
+void orc_das_dr(int S, int M, const double *re, const double *im, const double *C, double scale, double *b)
+{
+    for (int n = 0; n < S; ++n) {
+        double sr = 0.0;
+        for (int p = 0; p < M; ++p) {
+            double lpr = re[(size_t)n * M + p], lpi = -im[(size_t)n * M + p]; /* conj(l_p) */
+            for (int q = 0; q < M; ++q) {
+                if (q == p) continue;
+                double cr = C[2 * ((size_t)p * M + q)], ci = C[2 * ((size_t)p * M + q) + 1];
+                double lqr = re[(size_t)n * M + q], lqi = im[(size_t)n * M + q];
+                /* conj(l_p) * C_pq * l_q, real part */
+                double tr = lpr * cr - lpi * ci, ti = lpr * ci + lpi * cr;
+                sr += tr * lqr - ti * lqi;
+            }
+        }
+        b[n] = scale * sr;
+    }
+}
+
+void orc_psf_dr(int S, int M, const double *lre, const double *lim, const double *rre, const double *rim,
+                double scale, double *A, int lda)
+{
+    for (int n = 0; n < S; ++n) {
+        for (int s = 0; s < S; ++s) {
+            double acc = 0.0;
+            for (int m = 0; m < M; ++m) {
+                /* u = conj(l_nm) * r_sm */
+                double ur = lre[(size_t)n * M + m] * rre[(size_t)s * M + m] + lim[(size_t)n * M + m] * rim[(size_t)s * M + m];
+                double ui = lre[(size_t)n * M + m] * rim[(size_t)s * M + m] - lim[(size_t)n * M + m] * rre[(size_t)s * M + m];
+                for (int mp = 0; mp < M; ++mp) {
+                    if (mp == m) continue;
+                    /* w = conj(r_sm') * l_nm' ; term = u * w, real part */
+                    double wr = rre[(size_t)s * M + mp] * lre[(size_t)n * M + mp] + rim[(size_t)s * M + mp] * lim[(size_t)n * M + mp];
+                    double wi = rre[(size_t)s * M + mp] * lim[(size_t)n * M + mp] - rim[(size_t)s * M + mp] * lre[(size_t)n * M + mp];
+                    acc += ur * wr - ui * wi;
+                }
+            }
+            A[(size_t)n * lda + s] = scale * acc;
+        }
+    }
+}
+
+/*
  * DAMAS iteration, Eq. (13)-(14) (§3), x^0 given (the paper takes x^0 = 0):
  *   r_i = sum_{j<i} A_ij x_j^(n+1) + sum_{j>=i} A_ij x_j^(n) - b_i
  *   x_i^(n+1) = max(x_i^(n) - r_i / A_ii, 0),        i = 1..S in order.

@@ -186,3 +186,76 @@ def test_incoherent_superposition_equals_A_times_powers():
     x = np.zeros(sc.grid.S)
     x[sel] = pw * g2[sel]
     assert np.abs(A @ x - b).max() < 1e-12 * b.max()
+
+
+# ----------------------------------------------------------------------------- diagonal removal (§2)
+@pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
+def test_dr_map_of_uncorrelated_noise_is_zero(form):
+    """Removing the CSM diagonal removes any uncorrelated (diagonal) noise exactly."""
+    sc = synth.scene_monopole_small()
+    rng = np.random.default_rng(7)
+    C = np.diag(rng.uniform(0.1, 2.0, sc.M)).astype(complex)
+    b = O.das_map(sc.mics, sc.grid.points(), sc.freq, sc.c, C, form, diag_removal=True)
+    assert np.abs(b).max() == 0.0
+    b_full = O.das_map(sc.mics, sc.grid.points(), sc.freq, sc.c, C, form)
+    assert np.abs(b_full).min() > 0.0
+
+
+@pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
+def test_dr_psf_is_the_full_psf_less_the_pair_diagonal(form):
+    """The double sum over m != m' equals |sum_m conj(l_m) r_m|^2 - sum_m |l_m|^2 |r_m|^2
+    (a different computation: the full PSF and an explicit correction), and its
+    diagonal is 1 - sum_m |e_m|^4 (E) or 1 - 1/M (P)."""
+    sc = synth.scene_monopole_small()
+    pts = sc.grid.points()
+    A, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c, form)
+    Ad, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c, form, diag_removal=True)
+    if form == O.FORM_E:
+        L, _ = O.vectors(sc.mics, pts, sc.freq, sc.c, "e")
+        R, scale = L, 1.0
+    else:
+        L, _ = O.vectors(sc.mics, pts, sc.freq, sc.c, "v")
+        R, _ = O.vectors(sc.mics, pts, sc.freq, sc.c, "g")
+        scale = 1.0 / sc.M ** 2
+    corr = scale * (np.abs(L) ** 2) @ (np.abs(R) ** 2).T
+    assert np.allclose(Ad, A - corr, atol=1e-12, rtol=0)
+    want = 1.0 - (np.abs(L) ** 4).sum(1) if form == O.FORM_E else np.full(sc.grid.S, 1.0 - 1.0 / sc.M)
+    assert np.allclose(np.diag(Ad), want, atol=1e-12, rtol=0)
+
+
+def test_dr_psf_symmetric_psd_and_signed():
+    """Formulation E: a Gram matrix of the pair vectors (conj(e_m) e_m')_{m != m'}, so
+    symmetric PSD; unlike the full PSF it has negative entries."""
+    sc = synth.scene_monopole_small()
+    Ad, _ = O.psf_matrix(sc.mics, sc.grid.points(), sc.freq, sc.c, diag_removal=True)
+    assert np.array_equal(Ad, Ad.T)
+    assert np.linalg.eigvalsh(Ad).min() > -1e-12
+    assert (Ad < 0).any()
+
+
+@pytest.mark.parametrize("form", [O.FORM_E, O.FORM_P])
+def test_dr_map_of_an_on_grid_monopole_is_its_psf_column(form):
+    sc = synth.scene_monopole_small()
+    pts = sc.grid.points()
+    s = sc.grid.S // 2 + 3
+    g, g2 = O.vectors(sc.mics, pts[s:s + 1], sc.freq, sc.c, "g")
+    C = np.outer(g[0], np.conj(g[0]))
+    b = O.das_map(sc.mics, pts, sc.freq, sc.c, C, form, diag_removal=True)
+    Ad, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c, form, diag_removal=True)
+    col = Ad[:, s] * (g2[0] if form == O.FORM_E else 1.0)
+    assert np.allclose(b, col, atol=1e-12 * np.abs(col).max(), rtol=0)
+
+
+def test_gauss_seidel_unit_diagonal_rescaling():
+    """The clamped iteration on (A, b) equals, step for step, the one on
+    (D^-1/2 A D^-1/2, D^-1/2 b) with x = D^-1/2 y, D = diag(A): the update
+    x_i - r_i / A_ii becomes y_i - r'_i with r' = D^-1/2 r, and x >= 0 iff y >= 0."""
+    sc = synth.scene_monopole_small()
+    pts = sc.grid.points()
+    Ad, _ = O.psf_matrix(sc.mics, pts, sc.freq, sc.c, diag_removal=True)
+    b = O.das_map(sc.mics, pts, sc.freq, sc.c, sc.C, diag_removal=True)
+    d = np.sqrt(np.diag(Ad))
+    x = O.gauss_seidel(Ad, b, 40)
+    y = O.gauss_seidel(Ad / d[:, None] / d[None, :], b / d, 40)
+    assert np.abs(x).max() > 0
+    assert np.allclose(y / d, x, atol=1e-10 * np.abs(x).max(), rtol=0)
