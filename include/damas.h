@@ -81,6 +81,8 @@ typedef struct {
     double x0, y0, dx, dy, z; /* scan grid origin, spacing and plane distance (metres) */
     double c;                /* speed of sound c0 (m/s); k = 2 pi f / c0 (§2) */
     int formulation;         /* DAMAS_FORM_E or DAMAS_FORM_P */
+    int diag_removal;        /* 1: the CSM diagonal (auto-spectra) is removed (§2): das_map and
+                                damas_build_psf_dr drop the m = m' microphone pairs; 0: off */
 } damas_geom;
 
 #define DAMAS_MAX_MICS 256
@@ -122,6 +124,27 @@ int damas_state_floats(int S);
 int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev,
                     int S_sub, int a_dtype, void *A_dev, int lda, float *gnorm2_dev, damas_stream stream);
 
+/*
+ * PSF with the CSM diagonal removed (§2), for geom->diag_removal = 1 (which
+ * damas_build_psf rejects): the response at point n to a unit source at s
+ * without the m = m' microphone pairs,
+ *   A_ns = scale * ( |sum_m conj(l_nm) r_sm|^2 - sum_m |l_nm|^2 |r_sm|^2 ),
+ * whose diagonal d_n is no longer 1 and which has negative entries.  Returned
+ * rescaled to a unit diagonal, A'_ns = A_ns / (sqrt(d_n) sqrt(d_s)) (A'_nn = 1
+ * exactly), the form the solver takes: the clamped iteration on (A', b') with
+ * b'_n = b_n / sqrt(d_n) is, step for step, the one on (A, b) with
+ * x_n = x'_n / sqrt(d_n) (Eq. (14): the division by A_ii becomes the scaling).
+ *   A_dev       device float S_sub x lda (FP32 only).
+ *   gnorm2_dev  optional device float[S_sub]: ||g_n||^2 as in damas_build_psf.
+ *   dscale_dev  device float[S_sub]: sqrt(d_n).  damas_divide turns the
+ *               restricted map into b' and the solution x' into x.
+ */
+int damas_build_psf_dr(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev, int S_sub,
+                       float *A_dev, int lda, float *gnorm2_dev, float *dscale_dev, damas_stream stream);
+
+/* v[i] = v[i] / div[i], i < n (device arrays). */
+int damas_divide(damas_ctx *ctx, float *v_dev, const float *div_dev, int n, damas_stream stream);
+
 /* ------------------------------------------------------------------ a2: DAS map */
 
 /*
@@ -129,7 +152,8 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
  *   C_dev  device, M x M complex cross-spectral matrix (Eq. (1)), row-major,
  *          interleaved (re, im) FP32 pairs; assumed Hermitian.
  *   b_dev  device float[nx*ny] output, FP32, real part of v^H C v (scaled as
- *          the formulation says).
+ *          the formulation says); with geom->diag_removal the terms of the CSM
+ *          diagonal are left out.
  */
 int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float *C_dev, float *b_dev,
             damas_stream stream);

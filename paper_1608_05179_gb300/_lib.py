@@ -22,7 +22,7 @@ ERROR_NAMES = {0: "DAMAS_OK", -1: "DAMAS_EINVAL", -2: "DAMAS_ENOMEM", -3: "DAMAS
 class damas_geom(ctypes.Structure):
     _fields_ = [("M", c_int), ("mic_xyz_dev", c_void_p), ("nx", c_int), ("ny", c_int), ("x0", c_double),
                 ("y0", c_double), ("dx", c_double), ("dy", c_double), ("z", c_double), ("c", c_double),
-                ("formulation", c_int)]
+                ("formulation", c_int), ("diag_removal", c_int)]
 
 
 class damas_wavelet_cfg(ctypes.Structure):
@@ -68,6 +68,9 @@ SIGNATURES = {
     "damas_build_psf": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_int, c_void_p,
                                 c_int, c_void_p, c_void_p]),
     "das_map": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_void_p, c_void_p]),
+    "damas_build_psf_dr": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_void_p, c_int,
+                                   c_void_p, c_void_p, c_void_p]),
+    "damas_divide": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "wavelet_compress_grid": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(damas_wavelet_cfg), c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
     "wavelet_compress_grid_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(damas_wavelet_cfg),

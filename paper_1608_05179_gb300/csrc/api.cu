@@ -64,6 +64,9 @@ int check_geom(damas_ctx *ctx, const damas_geom *g) {
     if (!(g->c > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "speed of sound must be positive");
     if (g->formulation != DAMAS_FORM_E && g->formulation != DAMAS_FORM_P)
         return ctx_fail(ctx, DAMAS_EINVAL, "unknown formulation %d", g->formulation);
+    if (g->diag_removal != 0 && g->diag_removal != 1)
+        return ctx_fail(ctx, DAMAS_EINVAL, "diag_removal must be 0 or 1");
+    if (g->diag_removal && g->M < 2) return ctx_fail(ctx, DAMAS_EINVAL, "diagonal removal needs M >= 2");
     return DAMAS_OK;
 }
 
@@ -135,6 +138,8 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     int rc = check_geom(ctx, geom);
     if (rc) return rc;
     const long long S = (long long)geom->nx * geom->ny;
+    if (geom->diag_removal)
+        return ctx_fail(ctx, DAMAS_EINVAL, "diagonal removal: the PSF comes from damas_build_psf_dr");
     if (!(freq_hz > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "frequency must be positive");
     if (S_sub < 1 || S_sub > S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub=%d out of range", S_sub);
     if (!idx_dev && S_sub != S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub must equal nx*ny when idx is NULL");
@@ -161,6 +166,47 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     return DAMAS_OK;
 }
 
+int damas_build_psf_dr(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev, int S_sub,
+                       float *A_dev, int lda, float *gnorm2_dev, float *dscale_dev, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    int rc = check_geom(ctx, geom);
+    if (rc) return rc;
+    if (!geom->diag_removal) return ctx_fail(ctx, DAMAS_EINVAL, "damas_build_psf_dr needs geom->diag_removal = 1");
+    const long long S = (long long)geom->nx * geom->ny;
+    if (!(freq_hz > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "frequency must be positive");
+    if (S_sub < 1 || S_sub > S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub=%d out of range", S_sub);
+    if (!idx_dev && S_sub != S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub must equal nx*ny when idx is NULL");
+    if (!A_dev || !dscale_dev) return ctx_fail(ctx, DAMAS_EINVAL, "A_dev and dscale_dev are required");
+    if (lda < S_sub || lda % 32) return ctx_fail(ctx, DAMAS_EINVAL, "lda=%d must be a multiple of 32 and >= S_sub", lda);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ldm = planes_ld(geom->M);
+    const int nplanes = geom->formulation == DAMAS_FORM_P ? 4 : 2;
+    const size_t plane = (size_t)S_sub * ldm;
+    const size_t work = psf_work_floats(S_sub, ldm, nplanes == 2);
+    rc = ctx_ensure(ctx, ctx->planes, (plane * nplanes + work) * sizeof(float));
+    if (rc) return rc;
+    float *base = (float *)ctx->planes.ptr;
+    float *Lre = base, *Lim = base + plane;
+    float *Rre = nplanes == 4 ? base + 2 * plane : Lre, *Rim = nplanes == 4 ? base + 3 * plane : Lim;
+    GeomK gk = to_kernel(geom, freq_hz);
+    const int kind = geom->formulation == DAMAS_FORM_P ? 2 : 0;
+    DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, idx_dev, S_sub, Lre, Lim, Rre, Rim, ldm, gnorm2_dev, st));
+    const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
+    DAMAS_CUDA_TRY(ctx, launch_psf_gram(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, DAMAS_F32,
+                                        base + plane * nplanes, st));
+    DAMAS_CUDA_TRY(ctx, launch_psf_dr(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, dscale_dev, st));
+    return DAMAS_OK;
+}
+
+int damas_divide(damas_ctx *ctx, float *v_dev, const float *div_dev, int n, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (n < 0 || (n > 0 && (!v_dev || !div_dev))) return ctx_fail(ctx, DAMAS_EINVAL, "bad divide arguments");
+    DeviceGuard dg(ctx->device);
+    DAMAS_CUDA_TRY(ctx, launch_divide(v_dev, div_dev, n, (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
 // ----------------------------------------------------------------------------- DAS map
 int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float *C_dev, float *b_dev,
             damas_stream stream) {
@@ -182,7 +228,7 @@ int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float 
     const int kind = geom->formulation == DAMAS_FORM_P ? 1 : 0;
     DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, nullptr, S, Lre, Lim, nullptr, nullptr, ldm, nullptr, st));
     const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
-    DAMAS_CUDA_TRY(ctx, launch_das(Lre, Lim, ldm, geom->M, S, C_dev, scale, b_dev, st));
+    DAMAS_CUDA_TRY(ctx, launch_das(Lre, Lim, ldm, geom->M, S, C_dev, scale, b_dev, geom->diag_removal, st));
     return DAMAS_OK;
 }
 

@@ -65,9 +65,14 @@ cudaError_t launch_steer(const GeomK &g, int kind, const int32_t *idx, int n, fl
 cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm,
                             int M, int S, float scale, void *A, int lda, int a_dtype, float *work, cudaStream_t st);
 size_t psf_work_floats(int S, int ldm, bool symmetric);
-// b_n = scale * Re(L_n^H C L_n) for n < S.
+// b_n = scale * Re(L_n^H C L_n) for n < S (dr: without the terms of C's diagonal).
 cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,
-                       float *b, cudaStream_t st);
+                       float *b, int dr, cudaStream_t st);
+// Diagonal removal on a PSF the Gram wrote: d_n into dscale (as sqrt), then A
+// corrected and rescaled to a unit diagonal in place (FP32).
+cudaError_t launch_psf_dr(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm, int M,
+                          int S, float scale, float *A, int lda, float *dscale, cudaStream_t st);
+cudaError_t launch_divide(float *v, const float *d, int n, cudaStream_t st);
 cudaError_t launch_wavelet(const float *b, int nx, int ny, int levels, int pred, int eps_mode, float eps_abs,
                            float eps_rel, long long keep_K, int32_t *idx, int32_t *S_sub, float *detail,
                            float *eps_abs_out, float *work_absd, cudaStream_t st);

@@ -1,4 +1,5 @@
-// Mean-square DAS map (§2 Eq. (2)): b_n = scale * Re(l_n^H C l_n).
+// Mean-square DAS map (§2 Eq. (2)): b_n = scale * Re(l_n^H C l_n); with diagonal
+// removal (§2) the terms of the CSM diagonal are left out.
 //
 // Each warp takes grid points one after another: the point's vector l_n is put
 // in shared memory, lane p forms (C l_n)_p for p = lane, lane+32, ... from the
@@ -12,7 +13,8 @@ constexpr int DAS_THREADS = 256, DAS_WARPS = DAS_THREADS / 32, ROWS_PER_CHUNK = 
 
 __global__ void __launch_bounds__(DAS_THREADS) das_kernel(const float *__restrict__ Lre, const float *__restrict__ Lim,
                                                           int ldm, int M, int S, const float2 *__restrict__ C,
-                                                          float scale, float *__restrict__ b, int pts_per_warp) {
+                                                          float scale, float *__restrict__ b, int pts_per_warp,
+                                                          int dr) {
     extern __shared__ float2 sm[];
     const int cstride = M + 1;                       // padded row stride of the C chunk (float2)
     float2 *sC = sm;                                 // ROWS_PER_CHUNK x cstride
@@ -35,7 +37,8 @@ __global__ void __launch_bounds__(DAS_THREADS) das_kernel(const float *__restric
         __syncthreads();
         for (int e = threadIdx.x; e < rows * M; e += DAS_THREADS) {
             const int r = e / M, c = e % M;
-            sC[r * cstride + c] = C[(size_t)(p0 + r) * M + c];
+            // diagonal removal: the CSM diagonal enters as zero
+            sC[r * cstride + c] = (dr && c == p0 + r) ? make_float2(0.f, 0.f) : C[(size_t)(p0 + r) * M + c];
         }
         __syncthreads();
         for (int q = 0; q < pts_per_warp; ++q) {
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(DAS_THREADS) das_kernel(const float *__restric
 }  // namespace
 
 cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,
-                       float *b, cudaStream_t st) {
+                       float *b, int dr, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const int ppw = M <= 64 ? 8 : 4;
     const size_t smem = sizeof(float2) * ((size_t)ROWS_PER_CHUNK * (M + 1) + (size_t)DAS_WARPS * ppw * M);
@@ -76,6 +79,6 @@ cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S
     if (e != cudaSuccess) return e;
     const int pts_per_cta = DAS_WARPS * ppw;
     const int blocks = (S + pts_per_cta - 1) / pts_per_cta;
-    das_kernel<<<blocks, DAS_THREADS, smem, st>>>(Lre, Lim, ldm, M, S, (const float2 *)C, scale, b, ppw);
+    das_kernel<<<blocks, DAS_THREADS, smem, st>>>(Lre, Lim, ldm, M, S, (const float2 *)C, scale, b, ppw, dr);
     return cudaGetLastError();
 }

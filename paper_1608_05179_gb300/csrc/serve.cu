@@ -94,6 +94,7 @@ damas_geom job_geom(const Job &j) {
     g.z = j.req.z;
     g.c = j.req.c;
     g.formulation = j.req.formulation;
+    g.diag_removal = 0;
     return g;
 }
 

@@ -83,6 +83,7 @@ class Geometry:
     z: float
     c: float = 343.0
     formulation: int = FORM_E
+    diag_removal: int = 0      # 1: the CSM diagonal is removed (§2)
 
     @property
     def M(self):
@@ -94,12 +95,14 @@ class Geometry:
 
     def cstruct(self) -> _lib.damas_geom:
         return _lib.damas_geom(self.M, self.mic_xyz.data_ptr(), self.nx, self.ny, self.x0, self.y0, self.dx, self.dy,
-                               self.z, self.c, self.formulation)
+                               self.z, self.c, self.formulation, int(self.diag_removal))
 
     @staticmethod
-    def from_scene(mics: np.ndarray, grid, c: float, formulation: int = FORM_E, device="cuda") -> "Geometry":
+    def from_scene(mics: np.ndarray, grid, c: float, formulation: int = FORM_E, device="cuda",
+                   diag_removal: int = 0) -> "Geometry":
         m = torch.as_tensor(np.ascontiguousarray(mics, dtype=np.float64), device=device)
-        return Geometry(m, grid.nx, grid.ny, grid.x0, grid.y0, grid.dx, grid.dy, grid.z, c, formulation)
+        return Geometry(m, grid.nx, grid.ny, grid.x0, grid.y0, grid.dx, grid.dy, grid.z, c, formulation,
+                        int(diag_removal))
 
 
 def damas_lda(S: int) -> int:
@@ -126,6 +129,33 @@ def damas_build_psf(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor
     ctx.check(ctx.lib.damas_build_psf(ctx.handle, ctypes.byref(g), float(freq), _ptr(idx), int(S_sub), int(a_dtype),
                                       _ptr(A), int(A.shape[1]), _ptr(gnorm2), _stream(stream)))
     return A, gnorm2
+
+
+def damas_build_psf_dr(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor | None = None,
+                       S_sub: int | None = None, A: torch.Tensor | None = None, gnorm2: torch.Tensor | None = None,
+                       dscale: torch.Tensor | None = None, stream=None):
+    """PSF without the m = m' microphone pairs (diagonal removal, §2), rescaled to a
+    unit diagonal; returns (A', gnorm2, dscale = sqrt of the unscaled diagonal)."""
+    S_sub = geom.S if idx is None and S_sub is None else (S_sub if S_sub is not None else int(idx.numel()))
+    lda = damas_lda(S_sub)
+    dev = geom.mic_xyz.device
+    if A is None:
+        A = torch.empty((S_sub, lda), dtype=torch.float32, device=dev)
+    if gnorm2 is None:
+        gnorm2 = torch.empty(S_sub, dtype=torch.float32, device=dev)
+    if dscale is None:
+        dscale = torch.empty(S_sub, dtype=torch.float32, device=dev)
+    g = geom.cstruct()
+    ctx.check(ctx.lib.damas_build_psf_dr(ctx.handle, ctypes.byref(g), float(freq), _ptr(idx), int(S_sub), _ptr(A),
+                                         int(A.shape[1]), _ptr(gnorm2), _ptr(dscale), _stream(stream)))
+    return A, gnorm2, dscale
+
+
+def damas_divide(ctx: Context, v: torch.Tensor, div: torch.Tensor, n: int | None = None, stream=None):
+    """v[:n] /= div[:n] in place (FP32 device tensors)."""
+    n = int(v.numel()) if n is None else int(n)
+    ctx.check(ctx.lib.damas_divide(ctx.handle, _ptr(v), _ptr(div), n, _stream(stream)))
+    return v
 
 
 def das_map(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, b: torch.Tensor | None = None, stream=None):
@@ -258,9 +288,20 @@ def solve_bin(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, iters:
         b_sub = damas_gather(ctx, b, idx, S_sub, stream=stream)
     else:
         idx, S_sub, b_sub = None, geom.S, b
-    A, g2 = damas_build_psf(ctx, geom, freq, idx, S_sub, a_dtype, stream=stream)
+    if geom.diag_removal:
+        # unit-diagonal form of the system without the CSM diagonal: b' = b / sqrt(d), x = x' / sqrt(d)
+        if a_dtype != F32:
+            raise ValueError("diagonal removal builds A in FP32")
+        A, g2, dsc = damas_build_psf_dr(ctx, geom, freq, idx, S_sub, stream=stream)
+        if not compressed:
+            b_sub = b_sub.clone()
+        damas_divide(ctx, b_sub, dsc, S_sub, stream=stream)
+    else:
+        A, g2 = damas_build_psf(ctx, geom, freq, idx, S_sub, a_dtype, stream=stream)
     x = torch.empty(S_sub, dtype=torch.float32, device=b.device)
     damas_solve(ctx, System(A, b_sub, x, iters), stream=stream)
+    if geom.diag_removal:
+        damas_divide(ctx, x, dsc, S_sub, stream=stream)
     x_full, total = damas_scatter_power(ctx, x, idx, g2 if geom.formulation == FORM_E else None, S_sub, geom.S,
                                         stream=stream)
     return {"b": b, "idx": idx, "S_sub": S_sub, "A": A, "gnorm2": g2, "b_sub": b_sub, "x_sub": x, "x": x_full,

@@ -46,7 +46,7 @@ def test_struct_layouts_match_c():
 #include "damas.h"
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(damas_geom), sizeof(damas_wavelet_cfg), sizeof(damas_system), sizeof(damas_solve_cfg));
-  printf("%zu %zu %zu\n", offsetof(damas_geom, formulation), offsetof(damas_system, ctas), offsetof(damas_solve_cfg, a_placement));
+  printf("%zu %zu %zu %zu\n", offsetof(damas_geom, formulation), offsetof(damas_system, ctas), offsetof(damas_solve_cfg, a_placement), offsetof(damas_geom, diag_removal));
   return 0;
 }
 """
@@ -61,12 +61,13 @@ int main(void) {
     assert sizes == [ctypes.sizeof(_lib.damas_geom), ctypes.sizeof(_lib.damas_wavelet_cfg),
                      ctypes.sizeof(_lib.damas_system), ctypes.sizeof(_lib.damas_solve_cfg)]
     assert offs == [_lib.damas_geom.formulation.offset, _lib.damas_system.ctas.offset,
-                    _lib.damas_solve_cfg.a_placement.offset]
+                    _lib.damas_solve_cfg.a_placement.offset, _lib.damas_geom.diag_removal.offset]
 
 
 def test_host_only_entry_points(lib):
     assert lib.damas_lda(1) == 32 and lib.damas_lda(33) == 64 and lib.damas_lda(657) == 672
     assert lib.damas_lda(0) == 0
+    assert lib.damas_state_floats(100) == 264 and lib.damas_state_floats(0) == 0
 
 
 def test_create_rejects_bad_device(lib):
