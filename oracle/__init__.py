@@ -141,6 +141,27 @@ def das_map(mics, pts, freq, c, C, form: int = FORM_E, return_imag: bool = False
     return (b, bi) if return_imag else b
 
 
+def csm_welch(p, K: int, hop: int, bins):
+    """Cross-spectral matrix (Eq. (1)) of each FFT bin in `bins` estimated from
+    microphone time series p (M x T, FP64): blocks of K samples every `hop`
+    samples, periodic Hann window w, averaged over the L = (T - K) // hop + 1
+    blocks (Welch):
+        C_f = sum_l X_lf X_lf^H / (L * sum_t w(t)^2),
+        X_lf[m] = sum_t w(t) p[m, l*hop + t] exp(-2 pi i f t / K).
+    The FFT is numpy's (a library primitive used as one step)."""
+    p = np.asarray(p, np.float64)
+    M, T = p.shape
+    L = (T - K) // hop + 1
+    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(K) / K)
+    bins = np.asarray(bins, int)
+    C = np.zeros((len(bins), M, M), complex)
+    for l in range(L):
+        X = np.fft.fft(p[:, l * hop:l * hop + K] * w, axis=1)[:, bins]   # M x F
+        for i in range(len(bins)):
+            C[i] += np.outer(X[:, i], X[:, i].conj())
+    return C / (L * np.sum(w * w))
+
+
 def gauss_seidel(A, b, iters: int, x0=None):
     """DAMAS Gauss-Seidel with the non-negativity clamp, Eq. (13)-(14), FP64."""
     lib = _load()

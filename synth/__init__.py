@@ -117,6 +117,29 @@ def simulate_csm(mics: np.ndarray, src_xyz: np.ndarray, powers: np.ndarray, freq
     return 0.5 * (C + C.conj().T)
 
 
+def simulate_timeseries(mics: np.ndarray, src_xyz: np.ndarray, powers: np.ndarray, fs: float, T: int, c: float,
+                        snr_db: float | None, rng: np.random.Generator) -> np.ndarray:
+    """Microphone signals (M x T, float64) of incoherent monopoles emitting white
+    Gaussian noise of variance powers[s] per sample, each delayed by d/c and
+    scaled by |r_s|/d (the transfer of _transfer, so the expected CSM of a bin is
+    simulate_csm's); the delays are applied exactly (circularly) in the frequency
+    domain.  Plus white noise at snr_db below the mean signal power."""
+    mics = np.asarray(mics, float)
+    src = np.atleast_2d(np.asarray(src_xyz, float))
+    f = np.fft.rfftfreq(T, 1.0 / fs)
+    out = np.zeros((mics.shape[0], T))
+    for s_xyz, pw in zip(src, np.asarray(powers, float).reshape(-1)):
+        sig = np.fft.rfft(rng.standard_normal(T) * math.sqrt(pw))
+        d = np.sqrt(((s_xyz[None, :] - mics) ** 2).sum(1))
+        r0 = math.sqrt((s_xyz * s_xyz).sum())
+        for m in range(mics.shape[0]):
+            out[m] += (r0 / d[m]) * np.fft.irfft(sig * np.exp(-2j * math.pi * f * d[m] / c), T)
+    if snr_db is not None:
+        sig2 = 10.0 ** (-snr_db / 10.0) * float(np.mean(out * out))
+        out += rng.standard_normal(out.shape) * math.sqrt(sig2)
+    return out
+
+
 def csm_to_f32_interleaved(C: np.ndarray) -> np.ndarray:
     """Row-major M x M complex -> float32 array (M, M, 2) holding (re, im)."""
     out = np.empty(C.shape + (2,), np.float32)
