@@ -602,6 +602,35 @@ def run_eps(args):
             "eta_full_grid": round(eta_full, 4), "rows": rows}
 
 
+def run_csm(args):
+    """CSM estimation from time series (Welch): 64 microphones, 10 s at 51.2 kHz,
+    K = 1024 blocks with 50% overlap, 64 bins; the DFT of the selected bins is a
+    (M*L x K) x (K x 2F) product on CUDA cores."""
+    import torch
+    from paper_1608_05179_gb300 import damas as D
+    ctx = D.Context(0)
+    M, fs, T, K, hop, F = 64, 51200.0, 512000, 1024, 512, 64
+    rng = np.random.default_rng(6)
+    p = torch.as_tensor(rng.standard_normal((M, T)).astype(np.float32), device="cuda")
+    bins = torch.as_tensor(np.linspace(20, 480, F).astype(np.int32), device="cuda")
+    C = D.damas_csm(ctx, p, K, hop, bins)
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        D.damas_csm(ctx, p, K, hop, bins, C=C)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    L = (T - K) // hop + 1
+    flops = 2.0 * M * L * K * 2 * F + 8.0 * F * M * M * L
+    ctx.close()
+    return {"metric": "CSM from time series", "workload": f"M={M}, {T / fs:.0f} s at {fs:.0f} Hz, K={K}, hop={hop}, "
+            f"{F} bins, L={L} blocks", "ms": round(ms, 3), "samples_per_s": round(M * T / (ms / 1e3), 1),
+            "gflops": round(flops / (ms / 1e3) / 1e9, 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,7 +638,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="spiral81", choices=["spiral81", "band", "large", "serve", "psf", "eps"],
+    ap.add_argument("--workload", default="spiral81", choices=["spiral81", "band", "large", "serve", "psf", "eps", "csm"],
                     help="spiral81 is the benchmark line; the others print their own figures")
     ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = chosen by the autotuner)")
     ap.add_argument("--requests", type=int, default=32, help="serve: number of requests")
@@ -618,7 +647,7 @@ def main():
     if args.workload != "spiral81":
         from paper_1608_05179_gb300 import build as B
         B.build()
-        fn = {"band": run_band, "large": run_large, "serve": run_serve, "psf": run_psf, "eps": run_eps}[args.workload]
+        fn = {"band": run_band, "large": run_large, "serve": run_serve, "psf": run_psf, "eps": run_eps, "csm": run_csm}[args.workload]
         print(json.dumps(fn(args)))
         return
     args.warmup = max(args.warmup, 3)

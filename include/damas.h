@@ -158,6 +158,28 @@ int damas_divide(damas_ctx *ctx, float *v_dev, const float *div_dev, int n, dama
 int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float *C_dev, float *b_dev,
             damas_stream stream);
 
+/* ------------------------------------------------------------------ acquisition: CSM from time series */
+
+/*
+ * Cross-spectral matrix (Eq. (1)) of selected frequency bins estimated from
+ * microphone time series (Welch): blocks of K samples every hop samples,
+ * periodic Hann window w(t) = (1 - cos(2 pi t / K)) / 2, L = (T - K) / hop + 1
+ * blocks,
+ *   C_f = sum_l X_lf X_lf^H / (L * sum_t w(t)^2),
+ *   X_lf[m] = sum_t w(t) p[m][l*hop + t] exp(-2 pi i bins[f] t / K),
+ * so that a source of variance P per sample gives C = P a a^H for its transfer
+ * vector a, the form das_map takes (the same exp(-j k d) convention).
+ *   p_dev     device float[M][T] (row-major; T >= K).
+ *   bins_dev  device int32[F]: DFT bin indices, 0..K/2 (bin f is bins[f] * fs / K Hz).
+ *   C_dev     device float[F][M][M][2] output, interleaved (re, im), exactly Hermitian.
+ * Limits: M 1..DAMAS_MAX_MICS, K 2..1048576, hop >= 1, F 1..4096, M * L <= 4194240.
+ * The DFT of the selected bins runs as a tiled product of the sample blocks
+ * with a window-and-twiddle table (angles reduced exactly in integers, sine and
+ * cosine in FP64); products and sums in FP32.
+ */
+int damas_csm(damas_ctx *ctx, const float *p_dev, int M, long long T, int K, int hop, const int32_t *bins_dev,
+              int F, float *C_dev, damas_stream stream);
+
 /* ------------------------------------------------------------------ a3: compressed grid */
 
 typedef struct {

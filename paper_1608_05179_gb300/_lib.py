@@ -71,6 +71,8 @@ SIGNATURES = {
     "damas_build_psf_dr": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_void_p, c_int,
                                    c_void_p, c_void_p, c_void_p]),
     "damas_divide": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "damas_csm": (c_int, [c_void_p, c_void_p, c_int, ctypes.c_longlong, c_int, c_int, c_void_p, c_int, c_void_p,
+                          c_void_p]),
     "wavelet_compress_grid": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(damas_wavelet_cfg), c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
     "wavelet_compress_grid_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(damas_wavelet_cfg),

@@ -207,6 +207,26 @@ int damas_divide(damas_ctx *ctx, float *v_dev, const float *div_dev, int n, dama
     return DAMAS_OK;
 }
 
+// ----------------------------------------------------------------------------- CSM from time series
+int damas_csm(damas_ctx *ctx, const float *p_dev, int M, long long T, int K, int hop, const int32_t *bins_dev, int F,
+              float *C_dev, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (M < 1 || M > DAMAS_MAX_MICS) return ctx_fail(ctx, DAMAS_EINVAL, "M=%d out of range", M);
+    if (K < 2 || K > (1 << 20)) return ctx_fail(ctx, DAMAS_EINVAL, "K=%d out of range", K);
+    if (hop < 1) return ctx_fail(ctx, DAMAS_EINVAL, "hop must be >= 1");
+    if (T < K) return ctx_fail(ctx, DAMAS_EINVAL, "T=%lld shorter than one block", T);
+    if (F < 1 || F > 4096) return ctx_fail(ctx, DAMAS_EINVAL, "F=%d out of range", F);
+    if (!p_dev || !bins_dev || !C_dev) return ctx_fail(ctx, DAMAS_EINVAL, "NULL pointer");
+    const long long L = (T - K) / hop + 1;
+    if ((long long)M * L > 65535ll * 64) return ctx_fail(ctx, DAMAS_EINVAL, "M*L=%lld too large", (long long)M * L);
+    DeviceGuard dg(ctx->device);
+    const int rc = ctx_ensure(ctx, ctx->misc, csm_work_floats(M, (int)L, F, K) * sizeof(float));
+    if (rc) return rc;
+    DAMAS_CUDA_TRY(ctx, launch_csm(p_dev, M, T, K, hop, bins_dev, F, C_dev, (float *)ctx->misc.ptr,
+                                   (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
 // ----------------------------------------------------------------------------- DAS map
 int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float *C_dev, float *b_dev,
             damas_stream stream) {

@@ -73,6 +73,10 @@ cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S
 cudaError_t launch_psf_dr(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm, int M,
                           int S, float scale, float *A, int lda, float *dscale, cudaStream_t st);
 cudaError_t launch_divide(float *v, const float *d, int n, cudaStream_t st);
+// CSM of F bins from time series (Welch); work: csm_work_floats(M, L, F, K) floats.
+size_t csm_work_floats(int M, int L, int F, int K);
+cudaError_t launch_csm(const float *p, int M, long long T, int K, int hop, const int32_t *bins, int F, float *C,
+                       float *work, cudaStream_t st);
 cudaError_t launch_wavelet(const float *b, int nx, int ny, int levels, int pred, int eps_mode, float eps_abs,
                            float eps_rel, long long keep_K, int32_t *idx, int32_t *S_sub, float *detail,
                            float *eps_abs_out, float *work_absd, cudaStream_t st);

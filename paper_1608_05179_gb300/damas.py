@@ -158,6 +158,19 @@ def damas_divide(ctx: Context, v: torch.Tensor, div: torch.Tensor, n: int | None
     return v
 
 
+def damas_csm(ctx: Context, p: torch.Tensor, K: int, hop: int, bins: torch.Tensor, C: torch.Tensor | None = None,
+              stream=None):
+    """CSM (F, M, M, 2) of the DFT bins `bins` (int32 device tensor) from the time
+    series p (M, T) float32 on the device: Hann-windowed blocks of K samples every
+    hop samples, averaged (Welch)."""
+    M, T = int(p.shape[0]), int(p.shape[1])
+    F = int(bins.numel())
+    if C is None:
+        C = torch.empty((F, M, M, 2), dtype=torch.float32, device=p.device)
+    ctx.check(ctx.lib.damas_csm(ctx.handle, _ptr(p), M, T, int(K), int(hop), _ptr(bins), F, _ptr(C), _stream(stream)))
+    return C
+
+
 def das_map(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, b: torch.Tensor | None = None, stream=None):
     """DAS map of Eq. (2) on the full grid; C is (M, M, 2) float32 (re, im)."""
     if b is None:
