@@ -15,19 +15,21 @@
 // planes H (hi) and Lo (lo), one row per point, laid out per chunk of 16
 // microphones as [16 real parts | 16 imaginary parts] (128 bytes).
 // psf_gram_tc_kernel is persistent and warp specialised, one CTA per SM over a
-// list of 128 x 256 tiles of A (rows n, columns s):
-//   TMA thread (warp 9)    loads the chunk's four operand boxes (A hi/lo: 128
-//                          rows, B hi/lo: 256 rows; 128-byte swizzle) into a
-//                          two-stage ring                     -> full[st]
+// list of 128 x 128 tiles of A (rows n, columns s):
+//   TMA thread (warp 9)    loads the chunk's four operand boxes (A hi/lo, B
+//                          hi/lo: 128 rows each; 128-byte swizzle) into a
+//                          three-stage ring                   -> full[st]
 //   MMA thread (warp 8)    24 tcgen05.mma.cta_group::1.kind::tf32 per chunk
-//                          (M = 128, N = 256, K = 8; 3 split terms x 2 K slices
+//                          (M = 128, N = 128, K = 8; 3 split terms x 2 K slices
 //                          x {Re G += Lr.Rr, Re G += Li.Ri, Im G += Lr.Ri,
 //                          Im G -= Li.Rr via the negate-A bit}), accumulators
-//                          Re G and Im G in 512 TMEM columns  -> empty[st];
-//                          after a tile's last chunk            -> acc_full
-//   epilogue (warps 0-7)   waits acc_full, reads the accumulators 32 columns at
-//                          a time with tcgen05.ld (thread = tile row), writes
-//                          |G|^2                                -> acc_empty
+//                          Re G and Im G in 256 TMEM columns  -> empty[st];
+//                          after a tile's last chunk            -> acc_full[a]
+//   epilogue (warps 0-7)   waits acc_full[a], reads the accumulators 32 columns
+//                          at a time with tcgen05.ld (thread = tile row),
+//                          writes |G|^2                         -> acc_empty[a]
+// TMEM holds two accumulator slots (a = tile parity, 2 x 256 = 512 columns), so
+// the epilogue of one tile runs while the MMAs of the next fill the other slot.
 // The epilogue writes 32 x 32 blocks: the mirrored A[s][n] directly (the lanes
 // hold 32 consecutive n), the direct A[n][s] after a transpose through a
 // per-warp shared buffer, both as 128-byte warp stores.  For symmetric A (L and
@@ -51,21 +53,25 @@
 namespace {
 
 constexpr int BM = 128;           // tile rows (MMA M)
-constexpr int BN = 256;           // tile columns (MMA N)
+constexpr int BN = 128;           // tile columns (MMA N)
 constexpr int KC = 16;            // complex microphones per chunk
 constexpr int KR = 2 * KC;        // real K values per chunk: one 128-byte row
 constexpr int A_TILE = BM * KR * 4;              // 16 KB
-constexpr int B_TILE = BN * KR * 4;              // 32 KB
-constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands: 96 KB
-constexpr int NSTAGE = 2;
+constexpr int B_TILE = BN * KR * 4;              // 16 KB
+constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands: 64 KB
+constexpr int NSTAGE = 3;
 constexpr int EPI_WARPS = 8;                     // warps 0-7: epilogue, two per TMEM lane quarter
 constexpr int MMA_WARP = EPI_WARPS;              // warp 8: TMEM owner and MMA issuer
 constexpr int TMA_WARP = EPI_WARPS + 1;          // warp 9: operand loads
 constexpr int THREADS = 32 * (EPI_WARPS + 2);
 constexpr int TP_BYTES = EPI_WARPS * 32 * 32 * 4;  // per-warp 32 x 32 transpose buffers
 constexpr int SMEM_BYTES = NSTAGE * STAGE + TP_BYTES;
-constexpr uint32_t TMEM_COLS = 512;              // Re G in [0, 256), Im G in [256, 512)
+constexpr int NACC = 2;                           // accumulator slots in TMEM
+constexpr uint32_t ACC_COLS = 2 * BN;            // one slot: Re G in [0, BN), Im G in [BN, 2 BN)
+constexpr uint32_t TMEM_COLS = NACC * ACC_COLS;  // 512
 constexpr int TMA_BOX_ROWS = 128;
+static_assert(BM == TMA_BOX_ROWS && BN == TMA_BOX_ROWS, "one TMA box per operand tile");
+static_assert(SMEM_BYTES + 1024 <= 232448, "shared memory of one CTA");
 
 __device__ unsigned int psf_timeouts;
 
@@ -197,9 +203,12 @@ __global__ void __launch_bounds__(256) psf_split_kernel(const float *__restrict_
     Lo[o + 16] = to_tf32(im - hi);
 }
 
+// First column tile of row tile ty that reaches the upper triangle of a
+// symmetric A: s0 + BN - 1 >= n0 for s0 = tx BN, n0 = ty BM.
+__host__ __device__ __forceinline__ int first_upper_tile(int ty) { return ty * BM / BN; }
+
 // Tile t of the launch's tile list -> (row tile, column tile).  Symmetric A runs
-// the tiles that reach the upper triangle, s0 + BN - 1 >= n0, i.e. column tiles
-// tx >= ty / 2 in row tile ty (BN = 2 BM).
+// only the tiles that reach the upper triangle.
 __device__ __forceinline__ void tile_coords(int t, int ntx, int symmetric, int &ty, int &tx) {
     if (!symmetric) {
         ty = t / ntx;
@@ -208,12 +217,12 @@ __device__ __forceinline__ void tile_coords(int t, int ntx, int symmetric, int &
     }
     ty = 0;
     for (;;) {
-        const int cnt = ntx - (ty >> 1);
+        const int cnt = ntx - first_upper_tile(ty);
         if (t < cnt) break;
         t -= cnt;
         ++ty;
     }
-    tx = (ty >> 1) + t;
+    tx = first_upper_tile(ty) + t;
 }
 
 struct GramMaps {
@@ -225,7 +234,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     psf_gram_tc_kernel(const __grid_constant__ GramMaps maps, int M, int S, float scale, OutT *__restrict__ A,
                        int lda, int symmetric, int ntx, int ntiles, unsigned long long timeout_ns) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long full_bar[NSTAGE], empty_bar[NSTAGE], acc_full, acc_empty, done_bar;
+    __shared__ __align__(8) unsigned long long full_bar[NSTAGE], empty_bar[NSTAGE], acc_full[NACC], acc_empty[NACC],
+        done_bar;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -244,8 +254,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(smem_u32(&full_bar[i]), 1);
             mbar_init(smem_u32(&empty_bar[i]), 1);
         }
-        mbar_init(smem_u32(&acc_full), 1);
-        mbar_init(smem_u32(&acc_empty), 32 * EPI_WARPS);
+        for (int i = 0; i < NACC; ++i) {
+            mbar_init(smem_u32(&acc_full[i]), 1);
+            mbar_init(smem_u32(&acc_empty[i]), 32 * EPI_WARPS);
+        }
         mbar_init(smem_u32(&done_bar), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -265,15 +277,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == TMA_WARP) {
         if (lane == 0) {
-            uint32_t gch = 0;
+            // ring position: stage st in its use u (the u-th time it is filled)
+            int st = 0;
+            uint32_t u = 0;
             for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
                 int ty, tx;
                 tile_coords(t, ntx, symmetric, ty, tx);
                 const int n0 = ty * BM, s0 = tx * BN;
                 bool ok = true;
-                for (int c = 0; c < nchunk; ++c, ++gch) {
-                    const int st = gch & 1;
-                    if (gch >= NSTAGE && !wait(smem_u32(&empty_bar[st]), ((gch - NSTAGE) >> 1) & 1)) {
+                for (int c = 0; c < nchunk; ++c) {
+                    // the MMAs of use u - 1 of this stage must have read it
+                    if (u > 0 && !wait(smem_u32(&empty_bar[st]), (u - 1) & 1)) {
                         ok = false;
                         break;
                     }
@@ -282,11 +296,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     mbar_expect_tx(bar, STAGE);
                     tma_load_2d(stage, &maps.a_hi, x, n0, bar);
                     tma_load_2d(stage + A_TILE, &maps.a_lo, x, n0, bar);
-                    const uint32_t b = stage + 2 * A_TILE;
-                    tma_load_2d(b, &maps.b_hi, x, s0, bar);
-                    tma_load_2d(b + B_TILE / 2, &maps.b_hi, x, s0 + TMA_BOX_ROWS, bar);
-                    tma_load_2d(b + B_TILE, &maps.b_lo, x, s0, bar);
-                    tma_load_2d(b + B_TILE + B_TILE / 2, &maps.b_lo, x, s0 + TMA_BOX_ROWS, bar);
+                    tma_load_2d(stage + 2 * A_TILE, &maps.b_hi, x, s0, bar);
+                    tma_load_2d(stage + 2 * A_TILE + B_TILE, &maps.b_lo, x, s0, bar);
+                    if (++st == NSTAGE) {
+                        st = 0;
+                        ++u;
+                    }
                 }
                 if (!ok) break;
             }
@@ -294,15 +309,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
-            uint32_t gch = 0, k = 0;
+            int st = 0;
+            uint32_t u = 0, k = 0;
             bool issued = false;
             for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++k) {
-                if (k > 0 && !wait(smem_u32(&acc_empty), (k - 1) & 1)) break;
+                // slot a was last used by tile k - 2: its epilogue must have drained it
+                const int a = k & 1;
+                if (k >= NACC && !wait(smem_u32(&acc_empty[a]), ((k >> 1) - 1) & 1)) break;
                 fence_after();
+                const uint32_t d_re = tmem + a * ACC_COLS, d_im = d_re + BN;
                 bool ok = true;
-                for (int c = 0; c < nchunk; ++c, ++gch) {
-                    const int st = gch & 1;
-                    if (!wait(smem_u32(&full_bar[st]), (gch >> 1) & 1)) {
+                for (int c = 0; c < nchunk; ++c) {
+                    if (!wait(smem_u32(&full_bar[st]), u & 1)) {
                         ok = false;
                         break;
                     }
@@ -322,17 +340,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const uint64_t bre = smem_desc_sw128(b_ops[term] + 32 * j);
                             const uint64_t bim = smem_desc_sw128(b_ops[term] + 64 + 32 * j);
                             const uint32_t acc = (c == 0 && term == 0 && j == 0) ? 0u : 1u;
-                            mma_tf32(tmem, are, bre, IDESC, acc);             // Re G += Lr.Rr
-                            mma_tf32(tmem, aim, bim, IDESC, 1u);              // Re G += Li.Ri
-                            mma_tf32(tmem + BN, are, bim, IDESC, acc);        // Im G += Lr.Ri
-                            mma_tf32(tmem + BN, aim, bre, IDESC_NEG_A, 1u);   // Im G -= Li.Rr
+                            mma_tf32(d_re, are, bre, IDESC, acc);             // Re G += Lr.Rr
+                            mma_tf32(d_re, aim, bim, IDESC, 1u);              // Re G += Li.Ri
+                            mma_tf32(d_im, are, bim, IDESC, acc);             // Im G += Lr.Ri
+                            mma_tf32(d_im, aim, bre, IDESC_NEG_A, 1u);        // Im G -= Li.Rr
                         }
                     }
                     mma_commit(smem_u32(&empty_bar[st]));
                     issued = true;
+                    if (++st == NSTAGE) {
+                        st = 0;
+                        ++u;
+                    }
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(&acc_full));
+                mma_commit(smem_u32(&acc_full[a]));
             }
             // no MMA may still be running when TMEM is released
             if (issued) {
@@ -342,6 +364,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         __syncwarp();
     } else {
+        constexpr int CB = BN / 32 / 2;            // column blocks per warp
         const int q = warp & 3, half = warp >> 2;  // TMEM lane quarter, half of the column blocks
         float *tp = tp_all + warp * 32 * 32;       // element (r, c) at r * 32 + (c ^ r)
         const float nanv = __int_as_float(0x7fc00000);
@@ -351,10 +374,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             tile_coords(t, ntx, symmetric, ty, tx);
             const int nb = ty * BM + 32 * q;   // first row of this warp's 32 x 32 blocks
             const int n = nb + lane;           // this thread's row
-            const bool ok = wait(smem_u32(&acc_full), k & 1);
+            const int a = k & 1;
+            const bool ok = wait(smem_u32(&acc_full[a]), (k >> 1) & 1);
             fence_after();
 #pragma unroll 1
-            for (int cb = 4 * half; cb < 4 * half + 4; ++cb) {
+            for (int cb = CB * half; cb < CB * half + CB; ++cb) {
                 const int sb = tx * BN + 32 * cb;  // first column of the block
                 if (sb >= lda) break;
                 // symmetric A: blocks below the diagonal are written by their mirror
@@ -362,7 +386,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 float v[32];
                 if (ok) {
                     float gi[32];
-                    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cb);
+                    const uint32_t taddr = tmem + a * ACC_COLS + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cb);
                     tmem_ld32(taddr, v);
                     tmem_ld32(taddr + BN, gi);
                     tmem_ld_wait();
@@ -405,7 +429,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             fence_before();
-            mbar_arrive(smem_u32(&acc_empty));
+            mbar_arrive(smem_u32(&acc_empty[a]));
         }
         if (threadIdx.x == 0 && abort_flag) atomicAdd(&psf_timeouts, 1u);
     }
@@ -478,7 +502,7 @@ cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre
     const int ntx = (lda + BN - 1) / BN, nty = (S + BM - 1) / BM;
     long long ntiles = 0;
     if (symmetric)
-        for (int ty = 0; ty < nty; ++ty) ntiles += ntx - (ty >> 1) > 0 ? ntx - (ty >> 1) : 0;
+        for (int ty = 0; ty < nty; ++ty) ntiles += ntx - first_upper_tile(ty) > 0 ? ntx - first_upper_tile(ty) : 0;
     else
         ntiles = (long long)ntx * nty;
     if (ntiles <= 0) return cudaSuccess;

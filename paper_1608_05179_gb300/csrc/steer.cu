@@ -1,10 +1,15 @@
 // Steering / propagation vectors of scan-grid points (§2 Eq. (4), §3 Eq. (7)).
 //
-// One warp per point, lanes over microphones.  Distances and the phase k*d
-// are formed in FP64; the phase is reduced to the fraction of a period
-// t = d*f/c - rint(d*f/c) before an FP32 sin/cos of 2*pi*t, so the FP32 part
-// only sees an argument in [-pi, pi].  Time convention exp(+j w t): a wave
-// travelling distance d picks up exp(-j k d).
+// One warp per point, lanes over microphones.  The distance d and the phase
+// k*d are formed in FP64: d^2 from the FP64 coordinate differences, then
+// 1/d from an FP32 reciprocal-square-root seed y refined by one Newton step
+// for x^-1/2, y' = y (3/2 - d^2 y^2 / 2), which takes the seed's relative error
+// e (a few 1e-7) to about 1.5 e^2 (below 2e-13), and d = d^2 y'.  The phase is
+// reduced to the fraction of a period t = d*f/c - rint(d*f/c) before an FP32
+// sin/cos of 2*pi*t, so the FP32 part only sees an argument in [-pi, pi].  The
+// amplitude |r|/d = |r| y' and ||g||^2 are formed in FP64 without a division.
+// Time convention exp(+j w t): a wave travelling distance d picks up
+// exp(-j k d).
 #include "common.cuh"
 
 namespace {
@@ -14,6 +19,22 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Microphone m seen from point (px, py, pz): cos and sin of the phase
+// 2 pi (d f / c), the distance d and its reciprocal (FP64).
+__device__ __forceinline__ void mic_term(const GeomK &g, int m, double px, double py, double pz, float &c, float &s,
+                                         double &d, double &inv_d) {
+    const double ddx = px - g.mic[3 * m], ddy = py - g.mic[3 * m + 1], ddz = pz - g.mic[3 * m + 2];
+    const double d2 = fma(ddx, ddx, fma(ddy, ddy, ddz * ddz));
+    const double y = (double)rsqrtf((float)d2);
+    inv_d = fma(0.5 * y, fma(-d2 * y, y, 1.0), y);
+    d = d2 > 0.0 ? d2 * inv_d : 0.0;
+    double t = d * g.f_over_c;
+    t -= rint(t);
+    sincospif(2.0f * (float)t, &s, &c);
+}
+
+constexpr int MAX_CACHED = 8;  // microphone terms per lane kept in registers (M <= 256)
 
 // kind: 0 = L = g/||g|| (formulation E), 1 = L = v only, 2 = L = v and R = g (formulation P)
 __global__ void __launch_bounds__(256) steer_kernel(GeomK g, int kind, const int32_t *__restrict__ idx, int n_pts,
@@ -28,48 +49,70 @@ __global__ void __launch_bounds__(256) steer_kernel(GeomK g, int kind, const int
     const double px = g.x0 + ix * g.dx, py = g.y0 + iy * g.dy, pz = g.z;
     const double rabs = sqrt(px * px + py * py + pz * pz);
 
-    // ||g||^2 = sum_m (|r| / d_m)^2
+    // ||g||^2 = sum_m (|r| / d_m)^2; the terms of the first MAX_CACHED
+    // microphones of this lane stay in registers for the output pass
+    // (q = |r| / d, and d as FP32)
+    float cc[MAX_CACHED], ss[MAX_CACHED], qq[MAX_CACHED], dd[MAX_CACHED];
     double g2 = 0.0;
-    for (int m = lane; m < g.M; m += 32) {
-        const double ddx = px - g.mic[3 * m], ddy = py - g.mic[3 * m + 1], ddz = pz - g.mic[3 * m + 2];
-        const double d = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-        const double a = rabs / d;
-        g2 += a * a;
+#pragma unroll
+    for (int j = 0; j < MAX_CACHED; ++j) {
+        const int m = lane + 32 * j;
+        if (m < g.M) {
+            double d, inv_d;
+            mic_term(g, m, px, py, pz, cc[j], ss[j], d, inv_d);
+            const double a = rabs * inv_d;
+            g2 = fma(a, a, g2);
+            qq[j] = (float)a;
+            dd[j] = (float)d;
+        }
+    }
+    for (int m = lane + 32 * MAX_CACHED; m < g.M; m += 32) {
+        float c, s;
+        double d, inv_d;
+        mic_term(g, m, px, py, pz, c, s, d, inv_d);
+        const double a = rabs * inv_d;
+        g2 = fma(a, a, g2);
     }
     g2 = warp_sum_d(g2);
     const double inv_norm = 1.0 / sqrt(g2);
+    const float inv_norm_f = (float)inv_norm, inv_rabs = (float)(1.0 / rabs);
     if (gnorm2 && lane == 0) gnorm2[warp] = (float)g2;
 
     const size_t row = (size_t)warp * ldm;
-    for (int m = lane; m < ldm; m += 32) {
-        if (m >= g.M) {  // zero padding of the plane rows
-            Lre[row + m] = 0.f;
-            Lim[row + m] = 0.f;
-            if (kind == 2) {
-                Rre[row + m] = 0.f;
-                Rim[row + m] = 0.f;
-            }
-            continue;
-        }
-        const double ddx = px - g.mic[3 * m], ddy = py - g.mic[3 * m + 1], ddz = pz - g.mic[3 * m + 2];
-        const double d = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-        double t = d * g.f_over_c;
-        t -= rint(t);
-        float s, c;
-        sincospif(2.0f * (float)t, &s, &c);
+    // q = |r| / d, dfl = d
+    auto put = [&](int m, float c, float s, float q, float dfl) {
         if (kind == 0) {
-            const float amp = (float)((rabs / d) * inv_norm);
+            const float amp = q * inv_norm_f;
             Lre[row + m] = amp * c;
             Lim[row + m] = -amp * s;
         } else {
-            const float av = (float)(d / rabs);
+            const float av = dfl * inv_rabs;
             Lre[row + m] = av * c;
             Lim[row + m] = -av * s;
             if (kind == 2) {
-                const float ag = (float)(rabs / d);
-                Rre[row + m] = ag * c;
-                Rim[row + m] = -ag * s;
+                Rre[row + m] = q * c;
+                Rim[row + m] = -q * s;
             }
+        }
+    };
+#pragma unroll
+    for (int j = 0; j < MAX_CACHED; ++j) {
+        const int m = lane + 32 * j;
+        if (m < g.M) put(m, cc[j], ss[j], qq[j], dd[j]);
+    }
+    for (int m = lane + 32 * MAX_CACHED; m < g.M; m += 32) {
+        float c, s;
+        double d, inv_d;
+        mic_term(g, m, px, py, pz, c, s, d, inv_d);
+        put(m, c, s, (float)(rabs * inv_d), (float)d);
+    }
+    // zero padding of the plane rows
+    for (int m = g.M + lane; m < ldm; m += 32) {
+        Lre[row + m] = 0.f;
+        Lim[row + m] = 0.f;
+        if (kind == 2) {
+            Rre[row + m] = 0.f;
+            Rim[row + m] = 0.f;
         }
     }
 }
