@@ -578,7 +578,8 @@ def run_eps(args):
     on the paper's setup; for each threshold eps (relative to the map's maximum,
     linear prediction, J = 5), the compression ratio sigma = S / S~ and the error
     eta of the integrated power against the known source power, next to the
-    full-grid solve; 1000 sweeps each."""
+    full-grid solve; 1000 sweeps each.  Two more rows pad the compressed grid
+    with the neighbours of every kept point (damas_pad_grid)."""
     import torch
     from paper_1608_05179_gb300 import damas as D
     ctx = D.Context(0)
@@ -589,12 +590,13 @@ def run_eps(args):
     rows = []
     full = D.solve_bin(ctx, geom, sc.freq, C, 1000, compressed=False)
     eta_full = abs(float(full["total_power"].item()) - truth) / truth
-    for eps in (0.01, 0.05, 0.1, 0.2):
+    # pad = 0: Algorithm 1 as printed; pad = 1: every kept point's 8 neighbours added
+    for eps, pad in ((0.01, 0), (0.05, 0), (0.1, 0), (0.2, 0), (0.1, 1), (0.2, 1)):
         out = D.solve_bin(ctx, geom, sc.freq, C, 1000, compressed=True, levels=5, predictor=D.PRED_LINEAR,
-                          eps_mode=D.EPS_REL_MAX, eps=eps)
+                          eps_mode=D.EPS_REL_MAX, eps=eps, pad_radius=pad)
         eta = abs(float(out["total_power"].item()) - truth) / truth
-        rows.append({"eps": eps, "S_compressed": out["S_sub"], "sigma": round(sc.grid.S / out["S_sub"], 2),
-                     "eta": round(eta, 4)})
+        rows.append({"eps": eps, "pad_radius": pad, "S_compressed": out["S_sub"],
+                     "sigma": round(sc.grid.S / out["S_sub"], 2), "eta": round(eta, 4)})
     ctx.close()
     return {"metric": "compression ratio and integrated-power error vs threshold (Table 2 analogue)",
             "workload": "paper setup: M=60 (3-arm spiral, D=1 m), 50x50 grid over a 60 deg opening at 5 m, 3 kHz, "

@@ -236,6 +236,27 @@ int wavelet_compress_grid_noalloc(damas_ctx *ctx, const float *b_dev, int nx, in
                                   int32_t *idx_dev, int32_t *S_sub_dev, float *detail_dev, float *eps_abs_dev,
                                   damas_stream stream);
 
+/*
+ * Neighbour padding of a compressed grid.  An extension, not part of
+ * Algorithm 1: §5 reports that DAMAS on the compressed grid aliases more on an
+ * extended source because kept points lie further apart there, and its remedy
+ * is a smaller eps (a denser grid everywhere).  Padding instead adds every grid
+ * point within Chebyshev distance `radius` of a kept point, which gives the
+ * kept regions back their full spacing and leaves the rest of the grid sparse.
+ *   idx_dev      device int32[*S_sub_dev]: grid indices (any order, repeats
+ *                allowed; entries outside [0, nx*ny) are ignored).
+ *   S_sub_dev    device int32[1]: their number (a value outside [0, nx*ny] is
+ *                clamped to that range).
+ *   radius       0..8; 0 returns the input set sorted without repeats.
+ *   out_idx_dev  device int32[nx*ny] (capacity) output: the padded set, ascending.
+ *                May be the same buffer as idx_dev.
+ *   out_S_dev    device int32[1] output: its size.
+ * Limits: nx, ny in 1..65535, nx*ny <= 4194304.  The selection is integer work
+ * and deterministic.
+ */
+int damas_pad_grid(damas_ctx *ctx, int nx, int ny, const int32_t *idx_dev, const int32_t *S_sub_dev, int radius,
+                   int32_t *out_idx_dev, int32_t *out_S_dev, damas_stream stream);
+
 /* ------------------------------------------------------------------ a5, a7: restriction and scatter */
 
 /* dst[i] = src[idx[i]], i < n (b~ of Eq. (24)). */

@@ -206,6 +206,25 @@ def default_levels(N: int) -> int:
     return 1
 
 
+def pad_grid(idx, nx: int, ny: int, radius: int):
+    """Neighbour padding of a compressed grid (an extension of Algorithm 1 aimed
+    at the aliasing §5 reports on the compressed grid): every grid point within
+    Chebyshev distance radius of a listed point, ascending.  Entries outside the
+    grid are ignored.  Plain loops over the listed points and the offsets."""
+    S = nx * ny
+    keep = np.zeros(S, dtype=bool)
+    for p in np.asarray(idx, dtype=np.int64).ravel():
+        if p < 0 or p >= S:
+            continue
+        ix, iy = int(p) % nx, int(p) // nx
+        for dy in range(-radius, radius + 1):
+            for dx in range(-radius, radius + 1):
+                x, y = ix + dx, iy + dy
+                if 0 <= x < nx and 0 <= y < ny:
+                    keep[y * nx + x] = True
+    return np.nonzero(keep)[0].astype(np.int32)
+
+
 # ----------------------------------------------------------------------------- numpy helpers
 def restrict(b, idx):
     """b~ = b[idx] (Eq. (24))."""
@@ -242,18 +261,21 @@ def kkt_residual(A, b, x):
 
 
 def solve_bin(mics, grid, freq, c, C, iters, compressed: bool, levels=None,
-              predictor=PRED_HAAR, eps_mode=EPS_KEEP_FRAC, eps=0.1, form=FORM_E, b_f32=None):
+              predictor=PRED_HAAR, eps_mode=EPS_KEEP_FRAC, eps=0.1, form=FORM_E, b_f32=None, pad_radius=0):
     """One frequency bin end to end (§5 procedure): DAS map, optional wavelet
     compression (Algorithm 1), PSF matrix on the kept points, Gauss-Seidel from
     x^0 = 0, scatter to the full grid and convert to power.  b_f32, when given,
     is the FP32 map the grid selection is taken from (the selection is an FP32
-    decision); otherwise the FP64 map rounded to FP32 is used."""
+    decision); otherwise the FP64 map rounded to FP32 is used.  pad_radius > 0
+    adds the neighbours of the kept points (pad_grid)."""
     pts = grid.points()
     b = das_map(mics, pts, freq, c, C, form)
     if compressed:
         bsel = np.asarray(b, np.float32) if b_f32 is None else np.asarray(b_f32, np.float32)
         L = default_levels(grid.nx) if levels is None else levels
         idx, _, _, eps_abs = wavelet_select(bsel, grid.nx, grid.ny, L, predictor, eps_mode, eps)
+        if pad_radius:
+            idx = pad_grid(idx, grid.nx, grid.ny, pad_radius)
     else:
         idx, eps_abs = np.arange(grid.S, dtype=np.int32), None
     A, g2 = psf_matrix(mics, pts[idx], freq, c, form)

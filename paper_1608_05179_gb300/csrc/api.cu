@@ -118,7 +118,7 @@ int damas_destroy(damas_ctx *ctx) {
     {
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();
-        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc})
+        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc, &ctx->pad})
             if (b->ptr) cudaFree(b->ptr);
     }
     delete ctx;
@@ -279,6 +279,22 @@ int wavelet_compress_grid(damas_ctx *ctx, const float *b_dev, int nx, int ny, co
     DAMAS_CUDA_TRY(ctx, launch_wavelet(b_dev, nx, ny, J, cfg->predictor, cfg->eps_mode, (float)cfg->eps, (float)cfg->eps,
                                        K, idx_dev, S_sub_dev, detail_dev, eps_abs_dev, (float *)ctx->wave.ptr,
                                        (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
+int damas_pad_grid(damas_ctx *ctx, int nx, int ny, const int32_t *idx_dev, const int32_t *S_sub_dev, int radius,
+                   int32_t *out_idx_dev, int32_t *out_S_dev, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (!idx_dev || !S_sub_dev || !out_idx_dev || !out_S_dev)
+        return ctx_fail(ctx, DAMAS_EINVAL, "idx_dev, S_sub_dev, out_idx_dev, out_S_dev are required");
+    if (nx < 1 || ny < 1 || nx > 65535 || ny > 65535 || (long long)nx * ny > 4194304)
+        return ctx_fail(ctx, DAMAS_EINVAL, "grid %dx%d out of range", nx, ny);
+    if (radius < 0 || radius > 8) return ctx_fail(ctx, DAMAS_EINVAL, "radius=%d out of range", radius);
+    DeviceGuard dg(ctx->device);
+    const int rc = ctx_ensure(ctx, ctx->pad, (size_t)nx * ny);
+    if (rc) return rc;
+    DAMAS_CUDA_TRY(ctx, launch_pad_grid(nx, ny, idx_dev, S_sub_dev, radius, out_idx_dev, out_S_dev,
+                                        (unsigned char *)ctx->pad.ptr, (cudaStream_t)stream));
     return DAMAS_OK;
 }
 

@@ -26,6 +26,7 @@ struct damas_ctx {
     ScratchBuf solve;    // solver exchange buffers and flags
     ScratchBuf status;   // solver status words
     ScratchBuf misc;
+    ScratchBuf pad;      // neighbour-padding marks
     unsigned int epoch = 0;      // mailbox epoch of the solver exchange buffers
     struct ServeState *serve = nullptr;  // serving loop, when started
 };
@@ -77,6 +78,10 @@ cudaError_t launch_divide(float *v, const float *d, int n, cudaStream_t st);
 size_t csm_work_floats(int M, int L, int F, int K);
 cudaError_t launch_csm(const float *p, int M, long long T, int K, int hop, const int32_t *bins, int F, float *C,
                        float *work, cudaStream_t st);
+// Neighbour padding of a grid-index set (one CTA): marks (bytes, S of them)
+// is scratch.
+cudaError_t launch_pad_grid(int nx, int ny, const int32_t *idx, const int32_t *n_in, int radius, int32_t *out,
+                            int32_t *n_out, unsigned char *marks, cudaStream_t st);
 cudaError_t launch_wavelet(const float *b, int nx, int ny, int levels, int pred, int eps_mode, float eps_abs,
                            float eps_rel, long long keep_K, int32_t *idx, int32_t *S_sub, float *detail,
                            float *eps_abs_out, float *work_absd, cudaStream_t st);

@@ -183,6 +183,39 @@ __global__ void __launch_bounds__(WT) wavelet_kernel(const float *__restrict__ b
     }
 }
 
+// Neighbour padding: clear the marks, mark the (2r+1)^2 square around every
+// listed point (clipped to the grid; concurrent writes store the same byte),
+// then the same ordered compaction as above.  Every listed index is read before
+// the barrier that precedes the first write of out, so out may alias idx.
+__global__ void __launch_bounds__(WT) pad_grid_kernel(int nx, int ny, const int32_t *__restrict__ idx,
+                                                      const int32_t *__restrict__ n_in, int radius, int32_t *out,
+                                                      int32_t *__restrict__ n_out, unsigned char *__restrict__ marks) {
+    __shared__ int warp_sums[32];
+    const int S = nx * ny;
+    for (int n = threadIdx.x; n < S; n += WT) marks[n] = 0;
+    __syncthreads();
+    const int n = min(max(*n_in, 0), S);
+    for (int i = threadIdx.x; i < n; i += WT) {
+        const int p = idx[i];
+        if (p < 0 || p >= S) continue;
+        const int ix = p % nx, iy = p / nx;
+        const int x0 = max(ix - radius, 0), x1 = min(ix + radius, nx - 1);
+        const int y0 = max(iy - radius, 0), y1 = min(iy + radius, ny - 1);
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x) marks[y * nx + x] = 1;
+    }
+    __syncthreads();
+    const int chunk = (S + WT - 1) / WT;
+    const int lo = min(S, threadIdx.x * chunk), hi = min(S, lo + chunk);
+    int cnt = 0;
+    for (int q = lo; q < hi; ++q) cnt += marks[q];
+    int total;
+    int pos = block_excl_scan(cnt, warp_sums, total);
+    for (int q = lo; q < hi; ++q)
+        if (marks[q]) out[pos++] = q;
+    if (threadIdx.x == 0) *n_out = total;
+}
+
 __global__ void gather_kernel(const float *__restrict__ src, const int32_t *__restrict__ idx, int n,
                               float *__restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,6 +256,12 @@ cudaError_t launch_wavelet(const float *b, int nx, int ny, int levels, int pred,
                            float *eps_abs_out, float *work_absd, cudaStream_t st) {
     wavelet_kernel<<<1, WT, 0, st>>>(b, nx, ny, levels, pred, eps_mode, eps_abs, eps_rel, keep_K, idx, S_sub, detail,
                                       eps_abs_out, work_absd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_grid(int nx, int ny, const int32_t *idx, const int32_t *n_in, int radius, int32_t *out,
+                            int32_t *n_out, unsigned char *marks, cudaStream_t st) {
+    pad_grid_kernel<<<1, WT, 0, st>>>(nx, ny, idx, n_in, radius, out, n_out, marks);
     return cudaGetLastError();
 }
 

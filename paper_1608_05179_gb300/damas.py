@@ -215,6 +215,19 @@ def wavelet_compress_grid_noalloc(ctx: Context, b: torch.Tensor, nx: int, ny: in
     return idx, S_sub, detail, eps_abs
 
 
+def damas_pad_grid(ctx: Context, idx: torch.Tensor, S_sub: torch.Tensor, nx: int, ny: int, radius: int,
+                   out_idx: torch.Tensor | None = None, out_S: torch.Tensor | None = None, stream=None):
+    """Neighbour padding of a compressed grid (every point within Chebyshev
+    distance radius of a kept point).  Returns (out_idx capacity tensor, out_S
+    device tensor)."""
+    dev = idx.device
+    out_idx = torch.empty(nx * ny, dtype=torch.int32, device=dev) if out_idx is None else out_idx
+    out_S = torch.empty(1, dtype=torch.int32, device=dev) if out_S is None else out_S
+    ctx.check(ctx.lib.damas_pad_grid(ctx.handle, int(nx), int(ny), _ptr(idx), _ptr(S_sub), int(radius), _ptr(out_idx),
+                                     _ptr(out_S), _stream(stream)))
+    return out_idx, out_S
+
+
 def damas_gather(ctx: Context, src: torch.Tensor, idx: torch.Tensor, n: int, dst: torch.Tensor | None = None,
                  stream=None):
     dst = torch.empty(n, dtype=torch.float32, device=src.device) if dst is None else dst
@@ -288,14 +301,18 @@ def solve_mixed(ctx: Context, A_bf16: torch.Tensor, A_f32: torch.Tensor, b: torc
 # ----------------------------------------------------------------------------- one frequency bin
 def solve_bin(ctx: Context, geom: Geometry, freq: float, C: torch.Tensor, iters: int, compressed: bool = True,
               levels: int = 2, predictor: int = PRED_HAAR, eps_mode: int = EPS_KEEP_FRAC, eps: float = 0.1,
-              a_dtype: int = F32, stream=None):
+              a_dtype: int = F32, pad_radius: int = 0, stream=None):
     """The method for one bin (§5): DAS map, wavelet-compressed grid (Algorithm 1),
+    optionally padded with the neighbours within pad_radius of every kept point,
     PSF matrix of the kept points, Gauss-Seidel from x = 0, power map on the
     full grid.  One host synchronisation reads the compressed size."""
     b = das_map(ctx, geom, freq, C, stream=stream)
     if compressed:
         idx, S_sub_t, _, _ = wavelet_compress_grid(ctx, b, geom.nx, geom.ny, levels, predictor, eps_mode, eps,
                                                    stream=stream)
+        if pad_radius:
+            idx, S_sub_t = damas_pad_grid(ctx, idx, S_sub_t, geom.nx, geom.ny, pad_radius, out_idx=idx,
+                                          stream=stream)
         S_sub = int(S_sub_t.item())
         idx = idx[:S_sub]
         b_sub = damas_gather(ctx, b, idx, S_sub, stream=stream)
