@@ -425,10 +425,10 @@ def run_band(args):
            "S_f_min": min(grids.S_f), "S_f_max": max(grids.S_f), "S_f_sum": sum(grids.S_f)}
     for name, dt, elt in (("f32", D.F32, 4), ("bf16", D.BF16, 2)):
         if args.rows:
-            (rows, cap), tune = (args.rows, None), None
+            plan, tune = ("rows", args.rows, None), None
         else:
-            (rows, cap), tune = BD.autotune_rows(ctx, geom, freqs, grids, iters_probe=20, a_dtype=dt)
-        bs = BD.BandSolver(ctx, geom, freqs, grids.S_f, 1000, dt, rows_per_cta=rows, capacity=cap)
+            plan, tune = BD.autotune_rows(ctx, geom, freqs, grids, iters_probe=20, a_dtype=dt)
+        bs = BD.plan_solver(ctx, geom, freqs, grids.S_f, 1000, dt, plan)
         bs.capture(grids)
         for _ in range(2):
             bs.replay()
@@ -451,8 +451,10 @@ def run_band(args):
         bytes_ = sum(float(n) * n for n in grids.S_f) * elt * 1000
         out[name] = {"bins_per_s": round(64 / (ms / 1e3), 2), "ms_per_band": round(ms, 2), "solve_ms": round(solve_ms, 2),
                      "sweep_gbs": round(bytes_ / (solve_ms / 1e3) / 1e9, 1), "ctas": sum(bs.ctas),
-                     "rows_per_cta": rows, "cta_capacity": bs_cap(bs, cap),
-                     "autotune_s_per_20_sweeps": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tune.items()} if tune else None}
+                     "team_plan": f"{plan[0]} {plan[1]}", "cta_capacity": bs_cap(bs, plan[2]),
+                     "largest_bin_ctas": bs.ctas[int(np.argmax(grids.S_f))],
+                     "autotune_s_per_20_sweeps": {f"{k[0]} {k[1]} x{k[2]}": round(v, 4) for k, v in tune.items()}
+                     if tune else None}
     ctx.close()
     return out
 

@@ -10,6 +10,7 @@ step runs in the library's kernels; this module only sequences the calls.
 """
 from __future__ import annotations
 
+import heapq
 import math
 import time
 from dataclasses import dataclass, field
@@ -53,17 +54,46 @@ def team_sizes(S_f, rows_per_cta: int, capacity: int) -> list[int]:
     return P
 
 
+def team_sizes_balanced(S_f, capacity: int, r0: float) -> list[int]:
+    """CTAs per bin that even out the bins' solve times.  Step-time model: a
+    step of a team with R rows per CTA costs about 1 + R / r0 (a fixed part -
+    the 32-row solve, the barrier, the hand-over - plus the fold of the step's
+    dx into the CTA's rows), and a bin of nb blocks takes nb steps per sweep.
+    Every bin starts with one CTA; each further CTA goes to the bin with the
+    longest estimated time, up to one CTA per 32-row block and `capacity` CTAs
+    in all.  Small bins have short chains and keep few CTAs; the largest bins,
+    whose chains set the length of the launch, get the rest."""
+    F = len(S_f)
+    nb = [max(1, -(-int(s) // 32)) for s in S_f]
+    P = [1] * F
+
+    def cost(f):
+        return nb[f] * (1.0 + S_f[f] / P[f] / r0)
+
+    heap = [(-cost(f), f) for f in range(F) if nb[f] > 1]
+    heapq.heapify(heap)
+    left = capacity - F
+    while left > 0 and heap:
+        _, f = heapq.heappop(heap)
+        P[f] += 1
+        left -= 1
+        if P[f] < nb[f]:
+            heapq.heappush(heap, (-cost(f), f))
+    return P
+
+
 class BandSolver:
     """Phase 2 for a fixed set of compressed sizes: buffers, plan and (optionally) a captured graph."""
 
     def __init__(self, ctx: D.Context, geom: D.Geometry, freqs, S_f, iters: int, a_dtype: int = D.F32,
-                 rows_per_cta: int = 1024, capacity: int | None = None):
+                 rows_per_cta: int = 1024, capacity: int | None = None, balance_r0: float | None = None):
         self.ctx, self.geom, self.freqs, self.S_f, self.iters = ctx, geom, list(freqs), list(S_f), iters
         self.a_dtype = a_dtype
         dev = geom.mic_xyz.device
         dt = torch.float32 if a_dtype == D.F32 else torch.bfloat16
         cap = capacity or torch.cuda.get_device_properties(dev).multi_processor_count
-        self.ctas = team_sizes(self.S_f, rows_per_cta, cap)
+        self.ctas = (team_sizes_balanced(self.S_f, cap, balance_r0) if balance_r0
+                     else team_sizes(self.S_f, rows_per_cta, cap))
         self.A = [torch.empty((s, D.damas_lda(s)), dtype=dt, device=dev) for s in self.S_f]
         self.g2 = [torch.empty(s, dtype=torch.float32, device=dev) for s in self.S_f]
         self.b_sub = [torch.empty(s, dtype=torch.float32, device=dev) for s in self.S_f]
@@ -115,31 +145,44 @@ class BandSolver:
             raise D.DamasError(st, "band solve status")
 
 
+def plan_solver(ctx, geom, freqs, S_f, iters: int, a_dtype: int, plan) -> "BandSolver":
+    """BandSolver for a team plan (policy, value, capacity): ("rows", rows per CTA,
+    capacity) sizes teams in proportion to S_f; ("balance", r0, capacity) evens
+    out the bins' solve times (team_sizes_balanced)."""
+    policy, value, cap = plan
+    if policy == "rows":
+        return BandSolver(ctx, geom, freqs, S_f, iters, a_dtype, rows_per_cta=int(value), capacity=cap)
+    if policy == "balance":
+        return BandSolver(ctx, geom, freqs, S_f, iters, a_dtype, capacity=cap, balance_r0=float(value))
+    raise ValueError(f"unknown team policy {policy!r}")
+
+
 def autotune_rows(ctx, geom, freqs, grids: BandGrids, iters_probe: int = 20, a_dtype: int = D.F32,
-                  candidates=(256, 512, 1024, 2048), cta_per_sm=(1, 2)):
-    """Pick the team plan for this band - rows per CTA, and how many CTAs the
-    device is asked to hold at once (one or two per SM) - by timing a short solve
-    of each candidate.  Returns ((rows, capacity), {(rows, capacity): seconds})."""
+                  candidates=(256, 512, 1024, 2048), cta_per_sm=(1, 2), balance=(256, 1024, 4096)):
+    """Pick the team plan for this band by timing a short solve of each
+    candidate: teams in proportion to S_f at each rows-per-CTA candidate, or
+    balanced solve times at each r0 in `balance`, with the device asked to hold
+    one or two CTAs per SM.  Returns (plan, {plan: seconds}), plan = (policy,
+    value, capacity) as plan_solver takes it."""
     sms = torch.cuda.get_device_properties(geom.mic_xyz.device).multi_processor_count
     best, timings = None, {}
-    for per_sm in cta_per_sm:
-        for rows in candidates:
-            cap = per_sm * sms
-            bs = BandSolver(ctx, geom, freqs, grids.S_f, iters_probe, a_dtype, rows, capacity=cap)
-            bs.run(grids)
+    plans = [(pol, v, per_sm * sms) for per_sm in cta_per_sm
+             for pol, vals in (("rows", candidates), ("balance", balance)) for v in vals]
+    for plan in plans:
+        bs = plan_solver(ctx, geom, freqs, grids.S_f, iters_probe, a_dtype, plan)
+        bs.run(grids)
+        bs.check()
+        systems = bs.systems()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            D.damas_solve(ctx, systems, status=bs.status)
             bs.check()
-            systems = bs.systems()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            try:
-                D.damas_solve(ctx, systems, status=bs.status)
-                bs.check()
-            except D.DamasError:
-                continue  # this plan does not fit the device at once
-            key = (rows, cap)
-            timings[key] = time.perf_counter() - t0
-            if best is None or timings[key] < timings[best]:
-                best = key
+        except D.DamasError:
+            continue  # this plan does not fit the device at once
+        timings[plan] = time.perf_counter() - t0
+        if best is None or timings[plan] < timings[best]:
+            best = plan
     return best, timings
 
 

@@ -79,26 +79,20 @@ def test_batched_solve_matches_oracle(ctx):
         assert err <= 1e-4
 
 
-def test_team_sizes_fit_capacity():
-    S_f = [600, 1200, 9000, 14641, 3000]
-    P = B.team_sizes(S_f, 512, 148)
-    assert sum(P) <= 148 and all(p >= 1 for p in P)
-    P2 = B.team_sizes(S_f, 512, 10)
-    assert sum(P2) <= max(10, len(S_f)) and P2[3] >= P2[0]
-
-
 def test_autotuner_picks_a_candidate(ctx):
     mics, grid, freqs, Cs = _band(3)
     geom = D.Geometry.from_scene(mics, grid, synth.SPEED_OF_SOUND)
     C = torch.stack([D.csm_tensor(c) for c in Cs])
     grids = B.compress_band(ctx, geom, freqs, C, 4, D.PRED_LINEAR, D.EPS_REL_MAX, 2e-3)
     grids.S_f = [int(v) for v in grids.S_f_dev.cpu().tolist()]
-    best, timings = B.autotune_rows(ctx, geom, freqs, grids, iters_probe=5, candidates=(256, 1024))
+    best, timings = B.autotune_rows(ctx, geom, freqs, grids, iters_probe=5, candidates=(256, 1024),
+                                    balance=(512,))
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert best in timings and min(timings, key=timings.get) == best
-    assert {rows for rows, _ in timings} <= {256, 1024} and {cap for _, cap in timings} <= {sms, 2 * sms}
-    assert (256, sms) in timings and (1024, sms) in timings
+    assert {(p, v) for p, v, _ in timings} <= {("rows", 256), ("rows", 1024), ("balance", 512)}
+    assert {cap for _, _, cap in timings} <= {sms, 2 * sms}
+    assert ("rows", 256, sms) in timings and ("rows", 1024, sms) in timings and ("balance", 512, sms) in timings
     # the chosen plan solves the band like any other
-    bs = B.BandSolver(ctx, geom, freqs, grids.S_f, 30, D.F32, best[0], capacity=best[1])
+    bs = B.plan_solver(ctx, geom, freqs, grids.S_f, 30, D.F32, best)
     bs.run(grids)
     bs.check()
