@@ -6,7 +6,11 @@
 // block J).  A team of CTAs serves one system: CTA c owns a contiguous range of
 // blocks and keeps x and the residual r = A x - b of its rows in shared memory
 // (r as an unevaluated FP32 pair hi + lo), plus its rows of A when they fit
-// ("resident"); otherwise A is read from global memory (L2/HBM).
+// ("resident"); otherwise A is read from global memory (L2/HBM), and the two
+// chain tiles of each own block (its diagonal block and the block of columns
+// J-1) are copied into shared memory ahead of their solve: all of them once
+// when the CTA owns at most four blocks, else through a four-slot ring filled
+// three own blocks ahead.
 //
 // Step G, in every CTA of the team (one CTA barrier per step):
 //  - warp 0, if the CTA owns block J, solves its rows in order.  With
@@ -43,6 +47,7 @@ constexpr int SW_THREADS = 256;
 constexpr int UPD_WARPS = 6;
 constexpr int UPD_THREADS = 32 * UPD_WARPS;
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int TSLOTS = 4;  // chain-tile slots of a streamed CTA (power of two)
 
 __device__ __forceinline__ int upd_index(int warp) { return warp < 4 ? warp - 1 : warp - 2; }
 
@@ -70,6 +75,9 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// all but the N most recent copy groups of this thread have landed
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
@@ -508,8 +516,14 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
     float *xs = rl + T.R;
     float *bnd = xs + T.R;                   // per-row bound for candidate detection
     uint32_t *As = (uint32_t *)(bnd + T.R);  // resident rows of A
-    char *tiles = (char *)(bnd + T.R);       // or: two slots of two chain tiles
+    char *tiles = (char *)(bnd + T.R);       // or: TSLOTS slots of two chain tiles
     const int slot_bytes = 2 * 32 * T.tile_ld;
+    // Streamed A: the chain tiles of own blocks.  With at most TSLOTS own blocks
+    // they are loaded once and stay; otherwise a ring of TSLOTS slots is filled
+    // TSLOTS - 1 own blocks ahead, so a block's tiles have landed long before it
+    // is solved (own solve number q uses slot q mod TSLOTS).
+    const int nown = T.jb1 - T.jb0;
+    const bool ring = nown > TSLOTS;
 
     // ---- prologue
     if (RES) {
@@ -519,10 +533,14 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
             for (int v = lane; v < wpr; v += 32) As[(size_t)r * T.lds_w + v] = r < T.nrows ? src[v] : 0u;
         }
     }
-    int tile_blk0 = -1, tile_blk1 = -1;  // warp 0: the block whose tiles each slot holds
+    int slot_q = 0;   // warp 0: slot of the next own solve
+    int pf_slot = 0;  // slot and own index of the next ring prefetch
+    int pf_k = 0;
     if (!RES && warp == 0 && pipelined) {
-        prefetch_tiles<F32>(s, T, tiles, T.jb0);
-        tile_blk0 = T.jb0;
+        const int first = ring ? TSLOTS - 1 : nown;
+        for (int q = 0; q < first; ++q) prefetch_tiles<F32>(s, T, tiles + q * slot_bytes, T.jb0 + q);
+        pf_slot = first & (TSLOTS - 1);
+        pf_k = first;
     }
     for (int r = threadIdx.x; r < T.R; r += SW_THREADS) {
         const int i = T.row0 + r;
@@ -586,7 +604,7 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
     }
     if (pipelined)
         for (int Jb = T.jb0 + warp; Jb < T.jb1; Jb += SW_THREADS / 32) block_bound<F32, RES>(s, T, As, Jb, xs, bnd);
-    if (warp == 0 && tile_blk0 >= 0) cp_async_wait_all();
+    if (warp == 0 && !RES && pipelined) cp_async_wait_all();
     __syncthreads();
 
     // ---- steps
@@ -624,9 +642,11 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
             if (ownJ) {
                 const char *tl = tiles;
                 if (!RES) {
-                    if (tile_blk1 == J) tl = tiles + slot_bytes;
-                    cp_async_wait_all();
-                    __syncwarp();
+                    tl = tiles + (ring ? slot_q : J - T.jb0) * slot_bytes;
+                    if (ring) {
+                        cp_async_wait_group<TSLOTS - 2>();  // this block's group; later ones may fly
+                        __syncwarp();
+                    }
                 }
                 const float dk =
                     solve_block2<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, bnd, dprev, true, nonneg_all);
@@ -636,18 +656,13 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
                                    ((unsigned long long)epoch << 32) | __float_as_uint(dk));
                 dring[gi][lane] = dk;
                 make_list(dk, nzidx[gi], &nzcnt[gi]);
-                if (!RES) {
-                    // tiles of the next own block, into the other slot
-                    const int Jn = J + 1 < T.jb1 ? J + 1 : T.jb0;
-                    if (Jn != tile_blk0 && Jn != tile_blk1) {
-                        const bool into1 = tile_blk0 == J;
-                        __syncwarp();
-                        prefetch_tiles<F32>(s, T, tiles + (into1 ? slot_bytes : 0), Jn);
-                        if (into1)
-                            tile_blk1 = Jn;
-                        else
-                            tile_blk0 = Jn;
-                    }
+                if (!RES && ring) {
+                    // the slot just used takes the own block TSLOTS - 1 solves ahead
+                    __syncwarp();
+                    prefetch_tiles<F32>(s, T, tiles + pf_slot * slot_bytes, T.jb0 + pf_k);
+                    pf_slot = (pf_slot + 1) & (TSLOTS - 1);
+                    if (++pf_k == nown) pf_k = 0;
+                    slot_q = (slot_q + 1) & (TSLOTS - 1);
                 }
             } else {
                 const unsigned long long *mb = s.mbox + (size_t)J * 32 + lane;
@@ -790,7 +805,7 @@ size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident) {
     if (resident)
         b += (size_t)R * ((size_t)lda * elt / 4 + 1) * 4;
     else
-        b += (size_t)2 * 2 * 32 * (32 * elt + 16);
+        b += (size_t)TSLOTS * 2 * 32 * (32 * elt + 16);
     return b;
 }
 
