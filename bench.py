@@ -315,6 +315,7 @@ def run_gpu(args, rank, world, local_rank):
     sweep_f_ms = statistics.mean(f_sweep_ms)
     ach_f = bytes_f / (sweep_f_ms / 1e3) / 1e9
     traffic = _traffic_from_profiles()
+    latency = _handover_floor(D, ctx, S_sub, S, sweep_c_ms, sweep_f_ms)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -336,12 +337,30 @@ def run_gpu(args, rank, world, local_rank):
                                "traffic": traffic.get("sweep_spiral81_full"), "algorithmic_bytes_per_launch": bytes_f,
                                "launch_ms": round(sweep_f_ms, 3)},
         "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "latency_floor": latency,
         "batched": batched,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clock_info,
         "wall_s_compressed_region": round(wall, 3),
     }
     ctx.close()
+    return out
+
+
+def _handover_floor(D, ctx, S_sub, S, sweep_c_ms, sweep_f_ms):
+    """The sweeps' communication floor: a team of P CTAs hands the iteration from
+    CTA to CTA P times per sweep, each at least one one-way hand-over (measured
+    here with the library's probe between CTA 0 and every other CTA)."""
+    ns = sorted(D.damas_handover_probe(ctx, rounds=200))
+    med = ns[len(ns) // 2]
+    out = {"handover_ns_median": round(med, 1), "handover_ns_min": round(ns[0], 1), "handover_ns_max": round(ns[-1], 1),
+           "what": "iters x (CTA-to-CTA hand-overs per sweep) x median one-way hand-over, against the launch"}
+    for name, n, ms in (("compressed", S_sub, sweep_c_ms), ("full_grid", S, sweep_f_ms)):
+        ncta, rows, res = D.damas_solve_plan(ctx, n, D.F32)
+        floor = ITERS * (ncta if ncta > 1 else 0) * med / 1e6
+        out[name] = {"team_ctas": ncta, "rows_per_cta": rows, "blocks_per_sweep": -(-n // 32),
+                     "handovers_per_sweep": ncta if ncta > 1 else 0, "floor_ms": round(floor, 3),
+                     "launch_ms": round(ms, 3), "frac": round(floor / ms, 3)}
     return out
 
 

@@ -343,6 +343,35 @@ typedef struct {
 int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg,
                 damas_stream stream);
 
+/*
+ * The plan damas_solve would choose for one system of S rows (host only; no
+ * device work): CTAs in its team, rows per CTA, and whether the CTAs keep their
+ * rows of A in shared memory (1) or stream them (0).  ctas and a_placement mean
+ * what damas_solve_cfg's ctas_per_system and a_placement mean.  Blocks of 32
+ * rows are owned contiguously, so one sweep hands the iteration from CTA to CTA
+ * *ncta_out times when *ncta_out > 1.
+ */
+int damas_solve_plan(damas_ctx *ctx, int S, int lda, int a_dtype, int ctas, int a_placement, int *ncta_out,
+                     int *rows_per_cta_out, int *resident_out);
+
+/*
+ * Measurement aid, not part of the method: the one-way latency of handing a
+ * value from one CTA to another the way damas_solve's teams hand each block's dx
+ * to the next owner (a relaxed 64-bit store to global memory, polled with
+ * relaxed loads).  CTA 0 of a cooperative launch passes a counter back and forth
+ * with each of CTAs 1..npairs in turn, `rounds` times.
+ *   rounds     1..100000.
+ *   max_pairs  pairs to measure, capped at the SM count - 1 (>= 1).
+ *   timeout_us bound on every wait in microseconds (0: 2 s); a wait that runs out
+ *              makes the call return DAMAS_ETIMEDOUT (the device stays usable).
+ *   ns_host    host double[max_pairs] output: mean nanoseconds per one-way hand-over
+ *              for each pair.
+ *   n_pairs    host int output: pairs measured.
+ * Synchronises the stream.
+ */
+int damas_handover_probe(damas_ctx *ctx, int rounds, int max_pairs, int timeout_us, double *ns_host, int *n_pairs,
+                         damas_stream stream);
+
 /* ------------------------------------------------------------------ serving */
 
 /*

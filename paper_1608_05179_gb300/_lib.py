@@ -82,6 +82,10 @@ SIGNATURES = {
     "damas_scatter_power": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
                                     c_void_p]),
     "damas_solve": (c_int, [c_void_p, ctypes.POINTER(damas_system), c_int, ctypes.POINTER(damas_solve_cfg), c_void_p]),
+    "damas_solve_plan": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "damas_handover_probe": (c_int, [c_void_p, c_int, c_int, c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(c_int), c_void_p]),
     "damas_serve_start": (c_int, [c_void_p, ctypes.POINTER(damas_serve_cfg)]),
     "damas_serve_submit": (c_int, [c_void_p, ctypes.POINTER(damas_request), ctypes.POINTER(ctypes.c_uint64)]),
     "damas_serve_poll": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(damas_result)]),

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdamas.so")
-SOURCES = ["api.cu", "steer.cu", "psf.cu", "psf_dr.cu", "csm.cu", "das.cu", "wavelet.cu", "sweep.cu", "serve.cu"]
+SOURCES = ["api.cu", "steer.cu", "psf.cu", "psf_dr.cu", "csm.cu", "das.cu", "wavelet.cu", "sweep.cu", "serve.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -118,7 +118,7 @@ int damas_destroy(damas_ctx *ctx) {
     {
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();
-        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc, &ctx->pad})
+        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc, &ctx->pad, &ctx->probe})
             if (b->ptr) cudaFree(b->ptr);
     }
     delete ctx;
@@ -366,6 +366,48 @@ Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int pl
 }
 
 }  // namespace
+
+int damas_solve_plan(damas_ctx *ctx, int S, int lda, int a_dtype, int ctas, int a_placement, int *ncta_out,
+                     int *rows_per_cta_out, int *resident_out) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (S < 1 || lda < round_up(S, 32) || lda % 32) return ctx_fail(ctx, DAMAS_EINVAL, "S=%d, lda=%d", S, lda);
+    if (a_dtype != DAMAS_F32 && a_dtype != DAMAS_BF16) return ctx_fail(ctx, DAMAS_EINVAL, "a_dtype");
+    if (ctas < 0 || a_placement < 0 || a_placement > 2) return ctx_fail(ctx, DAMAS_EINVAL, "ctas or a_placement");
+    damas_system s;
+    memset(&s, 0, sizeof(s));
+    s.S = S;
+    s.lda = lda;
+    s.a_dtype = a_dtype;
+    const Plan pl = plan_system(ctx, s, ctas, a_placement, ctx->sm_count);
+    if (ncta_out) *ncta_out = pl.ncta;
+    if (rows_per_cta_out) *rows_per_cta_out = pl.R;
+    if (resident_out) *resident_out = pl.resident;
+    return DAMAS_OK;
+}
+
+int damas_handover_probe(damas_ctx *ctx, int rounds, int max_pairs, int timeout_us, double *ns_host, int *n_pairs,
+                         damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (rounds < 1 || rounds > 100000 || max_pairs < 1 || timeout_us < 0 || !ns_host || !n_pairs)
+        return ctx_fail(ctx, DAMAS_EINVAL, "bad probe arguments");
+    DeviceGuard dg(ctx->device);
+    const int npairs = std::min(max_pairs, ctx->sm_count - 1);
+    if (npairs < 1) return ctx_fail(ctx, DAMAS_EINVAL, "the device has one SM");
+    int rc = ctx_ensure(ctx, ctx->probe, handover_probe_bytes(npairs));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *ns_dev = nullptr;
+    int *status_dev = nullptr;
+    const unsigned long long timeout_ns = (timeout_us > 0 ? (unsigned long long)timeout_us : 2000000ull) * 1000ull;
+    DAMAS_CUDA_TRY(ctx, launch_handover_probe(ctx->probe.ptr, rounds, npairs, timeout_ns, st, &ns_dev, &status_dev));
+    int status = 0;
+    DAMAS_CUDA_TRY(ctx, cudaMemcpyAsync(ns_host, ns_dev, sizeof(double) * npairs, cudaMemcpyDeviceToHost, st));
+    DAMAS_CUDA_TRY(ctx, cudaMemcpyAsync(&status, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DAMAS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    *n_pairs = npairs;
+    if (status != 0) return ctx_fail(ctx, DAMAS_ETIMEDOUT, "a hand-over wait ran out");
+    return DAMAS_OK;
+}
 
 int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg, damas_stream stream) {
     if (!ctx) return DAMAS_EINVAL;

@@ -27,6 +27,7 @@ struct damas_ctx {
     ScratchBuf status;   // solver status words
     ScratchBuf misc;
     ScratchBuf pad;      // neighbour-padding marks
+    ScratchBuf probe;    // hand-over probe words
     unsigned int epoch = 0;      // mailbox epoch of the solver exchange buffers
     struct ServeState *serve = nullptr;  // serving loop, when started
 };
@@ -78,6 +79,11 @@ cudaError_t launch_divide(float *v, const float *d, int n, cudaStream_t st);
 size_t csm_work_floats(int M, int L, int F, int K);
 cudaError_t launch_csm(const float *p, int M, long long T, int K, int hop, const int32_t *bins, int F, float *C,
                        float *work, cudaStream_t st);
+// Hand-over latency probe: work must hold handover_probe_bytes(npairs) bytes
+// of device memory; out_ns / status point into it (npairs doubles, one int).
+size_t handover_probe_bytes(int npairs);
+cudaError_t launch_handover_probe(void *work, int rounds, int npairs, unsigned long long timeout_ns, cudaStream_t st,
+                                  double **out_ns, int **status);
 // Neighbour padding of a grid-index set (one CTA): marks (bytes, S of them)
 // is scratch.
 cudaError_t launch_pad_grid(int nx, int ny, const int32_t *idx, const int32_t *n_in, int radius, int32_t *out,

@@ -285,6 +285,27 @@ def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int
     return systems
 
 
+def damas_solve_plan(ctx: Context, S: int, a_dtype: int = F32, ctas: int = 0, a_placement: int = PLACE_AUTO,
+                     lda: int | None = None):
+    """The team damas_solve would use for one system: (CTAs, rows per CTA, resident)."""
+    n, r, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ctx.check(ctx.lib.damas_solve_plan(ctx.handle, int(S), int(damas_lda(S) if lda is None else lda), int(a_dtype),
+                                       int(ctas), int(a_placement), ctypes.byref(n), ctypes.byref(r),
+                                       ctypes.byref(res)))
+    return n.value, r.value, bool(res.value)
+
+
+def damas_handover_probe(ctx: Context, rounds: int = 100, max_pairs: int = 1 << 30, timeout_us: int = 0,
+                         stream=None) -> list[float]:
+    """One-way CTA-to-CTA hand-over latency in ns, one value per CTA paired with CTA 0."""
+    cap = max(1, min(int(max_pairs), 4096))
+    buf = (ctypes.c_double * cap)()
+    n = ctypes.c_int()
+    ctx.check(ctx.lib.damas_handover_probe(ctx.handle, int(rounds), cap, int(timeout_us), buf, ctypes.byref(n),
+                                           _stream(stream)))
+    return [buf[i] for i in range(n.value)]
+
+
 def solve_mixed(ctx: Context, A_bf16: torch.Tensor, A_f32: torch.Tensor, b: torch.Tensor, x: torch.Tensor,
                 iters_bulk: int, iters_refine: int, stream=None, **kw):
     """Mixed-precision schedule: iters_bulk sweeps with A stored in BF16 (half the
