@@ -34,6 +34,8 @@
 //    rows receives dx_{J-1} one step later, just before dx_J, so every row sees
 //    every dx in step order.  Warp 4 only joins the barriers, leaving warp 0's
 //    scheduler to it.
+// Teams of equal size (2..16 CTAs) are launched as one thread-block cluster
+// each, so each team runs on one die; otherwise the launch is cooperative.
 // Systems of one block run the same steps without the overlap.  At the end x,
 // the residual and the two dx blocks not yet folded into every row are written
 // out, so a later call continues bit for bit.
@@ -818,6 +820,33 @@ cudaError_t sweep_occupancy(size_t smem, int *blocks_per_sm) {
 cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(damas_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // Teams only wait on their own members.  When every team has the same size
+    // (2..16 CTAs) the launch is one thread-block cluster per team: a cluster is
+    // co-scheduled on one GPC, so a team's hand-overs stay on one die (one-way
+    // hand-overs between SMs of different dies take about 1.7 times as long).
+    // Only when the device holds every cluster at once; otherwise the launch is
+    // cooperative as below.
+    bool same = p.nsys >= 1 && p.sys[0].ncta >= 2 && p.sys[0].ncta <= 16;
+    for (int i = 1; same && i < p.nsys; ++i) same = p.sys[i].ncta == p.sys[0].ncta;
+    if (same && grid == p.nsys * p.sys[0].ncta &&
+        cudaFuncSetAttribute(damas_sweep_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cc = {};
+        cc.gridDim = dim3(grid);
+        cc.blockDim = dim3(SW_THREADS);
+        cc.dynamicSmemBytes = smem;
+        cc.stream = st;
+        cudaLaunchAttribute ca[1];
+        ca[0].id = cudaLaunchAttributeClusterDimension;
+        ca[0].val.clusterDim.x = p.sys[0].ncta;
+        ca[0].val.clusterDim.y = 1;
+        ca[0].val.clusterDim.z = 1;
+        cc.attrs = ca;
+        cc.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, damas_sweep_kernel, &cc) == cudaSuccess && ncl >= p.nsys)
+            return cudaLaunchKernelEx(&cc, damas_sweep_kernel, p);
+        cudaGetLastError();  // a refused cluster query leaves no error behind
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(SW_THREADS);
