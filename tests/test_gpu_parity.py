@@ -397,6 +397,30 @@ def test_batched_systems_equal_solo(ctx):
         assert torch.equal(a.x, s.x)
 
 
+def test_equal_teams_one_cluster_each(ctx):
+    """Systems whose teams have the same size run as one thread-block cluster per
+    team: each result equals the same system solved alone (cooperative or one
+    cluster) and under a forced cooperative-sized team of another size, bit for bit,
+    and matches the oracle iteration."""
+    rng = np.random.default_rng(12)
+    made = [synth.random_psd_system(rng, S) for S in (300, 290, 310, 257, 280, 300)]
+    for ctas in (0, 3, 5):
+        systems, solo = [], []
+        for A64, b64 in made:
+            A = padded(A64)
+            b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+            systems.append(D.System(A, b, torch.zeros(len(b64), device="cuda"), 120, ctas=ctas))
+            solo.append(D.System(A, b, torch.zeros(len(b64), device="cuda"), 120))
+        sizes = {D.damas_solve_plan(ctx, s.b.numel(), ctas=ctas)[0] for s in systems}
+        assert len(sizes) == 1 and min(sizes) >= 2   # one team size: the clustered launch
+        D.damas_solve(ctx, systems)
+        for s in solo:
+            D.damas_solve(ctx, s)
+        for (A64, b64), a, s in zip(made, systems, solo):
+            assert torch.equal(a.x, s.x)
+            assert rel_l2(a.x.cpu().numpy(), _oracle_fp32_inputs(A64, b64, 120)) <= 1e-4
+
+
 def test_sweep_wait_timeout_reports_status_and_context_survives(ctx):
     """A withheld block flag makes the other CTAs' bounded waits run out: the
     call reports DAMAS_ETIMEDOUT, no GPU fault, and the next solve is correct."""
