@@ -128,14 +128,14 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
     return world * units_per_rank / (max_ms / 1e3)
 
 
-BATCH_BINS = 13
+BATCH_BINS = 26   # ~11-CTA teams; streamed, two CTAs per SM hold 26 of them in one launch
 
 
 def batched_leg(ctx, D, dev, K: int, reps: int = 3):
     """K independent bins of the 81x81 workload (scene seeds 100..100+K-1) through
     the whole path, their K systems solved in one persistent launch; compressed and
-    full grid.  A compressed bin's solve occupies about 11 SMs, so one launch holds
-    K of them side by side."""
+    full grid.  A compressed bin's team has about 11 CTAs; the solver streams the
+    teams' rows of A when that lets all K run side by side (two CTAs per SM)."""
     import torch
     scenes = [synth.scene_spiral_81(seed=100 + i) for i in range(K)]
     geoms = [D.Geometry.from_scene(sc.mics, sc.grid, sc.c, device=dev) for sc in scenes]

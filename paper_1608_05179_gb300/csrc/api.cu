@@ -436,8 +436,37 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
 
     // plan every system, then pack them into launches that fit on the device at once
     std::vector<Plan> plans(nsys);
-    for (int i = 0; i < nsys; ++i) {
+    for (int i = 0; i < nsys; ++i)
         plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement, ctx->sm_count);
+    if (placement == 0 && nsys > 1) {
+        // A batch whose resident teams need more than one launch (a resident CTA
+        // fills an SM) but whose streamed teams fit in one (two CTAs per SM) is
+        // streamed: the teams then run side by side.  Results do not depend on the
+        // placement.
+        auto fits_once = [&](const std::vector<Plan> &pl) -> bool {
+            size_t smem = 0;
+            int ctas = 0;
+            for (const Plan &q : pl) {
+                smem = std::max(smem, q.smem);
+                ctas += q.ncta;
+            }
+            int occ = 0;
+            if (nsys > SWEEP_MAX_SYS || sweep_occupancy(smem, &occ) != cudaSuccess) return false;
+            return ctas <= occ * ctx->sm_count;
+        };
+        bool any_res = false;
+        for (const Plan &q : plans) any_res |= q.resident != 0;
+        if (any_res && !fits_once(plans)) {
+            std::vector<Plan> streamed(nsys);
+            for (int i = 0; i < nsys; ++i)
+                streamed[i] = plans[i].resident
+                                  ? plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, 2, ctx->sm_count)
+                                  : plans[i];
+            if (fits_once(streamed)) plans.swap(streamed);
+        }
+        cudaGetLastError();
+    }
+    for (int i = 0; i < nsys; ++i) {
         if (plans[i].smem > ctx->smem_optin - 1024)
             return ctx_fail(ctx, DAMAS_EINVAL, "system %d: %zu bytes of shared memory per CTA do not fit", i,
                             plans[i].smem);

@@ -15,7 +15,7 @@ struct SweepSys {
     unsigned epoch0;
 };
 
-constexpr int SWEEP_MAX_SYS = 24;
+constexpr int SWEEP_MAX_SYS = 64;  // systems per launch (the parameter block stays far below 32 KB)
 
 struct SweepParams {
     SweepSys sys[SWEEP_MAX_SYS];
@@ -24,6 +24,7 @@ struct SweepParams {
     unsigned long long timeout_ns;
     int withhold_block;  // test hook: block index never published, or -1
 };
+static_assert(sizeof(SweepParams) <= 32000, "kernel parameter block");
 
 // shared memory a CTA needs for R rows (resident: its rows of A; otherwise chain tiles only)
 size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident);

@@ -397,6 +397,31 @@ def test_batched_systems_equal_solo(ctx):
         assert torch.equal(a.x, s.x)
 
 
+def test_large_batch_streamed_equals_solo(ctx):
+    """A batch whose resident teams would need more than one launch is streamed so
+    that all teams run side by side; every system still equals its solo solve (held
+    in shared memory) bit for bit."""
+    rng = np.random.default_rng(21)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    S = 600
+    n, R, res = D.damas_solve_plan(ctx, S)
+    assert res
+    k = sms // n + 2                       # more resident CTAs than SMs
+    made = [synth.random_psd_system(rng, S) for _ in range(k)]
+    systems, solo = [], []
+    for A64, b64 in made:
+        A = padded(A64)
+        b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+        systems.append(D.System(A, b, torch.zeros(S, device="cuda"), 100))
+        solo.append(D.System(A, b, torch.zeros(S, device="cuda"), 100))
+    D.damas_solve(ctx, systems)
+    for s_ in solo:
+        D.damas_solve(ctx, s_)
+    for (A64, b64), a, s_ in zip(made, systems, solo):
+        assert torch.equal(a.x, s_.x)
+    assert rel_l2(systems[0].x.cpu().numpy(), _oracle_fp32_inputs(*made[0], 100)) <= 1e-4
+
+
 def test_equal_teams_one_cluster_each(ctx):
     """Systems whose teams have the same size run as one thread-block cluster per
     team: each result equals the same system solved alone (cooperative or one
