@@ -560,7 +560,7 @@ def _serve_stream(D, SV, ctx, specs, full: bool):
         Cs = np.stack([synth.simulate_csm(scn.mics, scn.src_xyz, scn.powers, f, scn.c, 20.0, rng) for f in freqs])
         L = 0 if full else {41: 3, 81: 4, 121: 3, 161: 5}[sp["N"]]
         reqs.append(SV.Request(scn.mics, scn.grid, freqs, Cs, iters=1000, levels=L, eps=sp["keep_frac"]))
-    srv = SV.Server(ctx, max_inflight=8)
+    srv = SV.Server(ctx)   # library defaults: 32 in flight, 768 rows per CTA
     t0 = time.perf_counter()
     tickets = []
     for sp, r in zip(specs, reqs):

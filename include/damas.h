@@ -385,9 +385,9 @@ int damas_handover_probe(damas_ctx *ctx, int rounds, int max_pairs, int timeout_
  */
 typedef struct {
     size_t hbm_budget_bytes; /* device memory the loop may hold for requests; 0 = half the free memory */
-    int max_inflight;        /* requests on the device at once; 0 = 8 */
+    int max_inflight;        /* requests on the device at once; 0 = 32 */
     int sm_slots;            /* CTAs that concurrent solves may hold together; 0 = twice the SM count */
-    int rows_per_cta;        /* solver team size target, rows per CTA; 0 = 512 */
+    int rows_per_cta;        /* solver team size target, rows per CTA; 0 = 768 */
 } damas_serve_cfg;
 
 typedef struct {
