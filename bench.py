@@ -131,36 +131,62 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
 BATCH_BINS = 26   # ~11-CTA teams; streamed, two CTAs per SM hold 26 of them in one launch
 
 
-def batched_leg(ctx, D, dev, K: int, reps: int = 3):
+def batched_leg(ctx, D, dev, K: int, reps: int = 3, lanes: int = 4):
     """K independent bins of the 81x81 workload (scene seeds 100..100+K-1) through
     the whole path, their K systems solved in one persistent launch; compressed and
     full grid.  A compressed bin's team has about 11 CTAs; the solver streams the
-    teams' rows of A when that lets all K run side by side (two CTAs per SM)."""
+    teams' rows of A when that lets all K run side by side (two CTAs per SM).  The
+    per-bin steps before the solve (DAS map, grid selection, restriction, PSF) run
+    on `lanes` streams, each with its own library context (a context's scratch
+    serves one stream at a time)."""
     import torch
     scenes = [synth.scene_spiral_81(seed=100 + i) for i in range(K)]
     geoms = [D.Geometry.from_scene(sc.mics, sc.grid, sc.c, device=dev) for sc in scenes]
     Cs = [D.csm_tensor(sc.C, device=dev) for sc in scenes]
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     S = scenes[0].grid.S
+    pool = [ctx] + [D.Context(dev.index or 0) for _ in range(lanes - 1)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(lanes)]
+
+    def fan_out():
+        main = torch.cuda.current_stream(dev)
+        for st in streams:
+            st.wait_stream(main)
+
+    def fan_in():
+        main = torch.cuda.current_stream(dev)
+        for st in streams:
+            main.wait_stream(st)
 
     def run(compressed):
         systems, post = [], []
-        bs = [D.das_map(ctx, g, sc.freq, C) for g, sc, C in zip(geoms, scenes, Cs)]
+        fan_out()
+        bs, sel = [], []
+        for i, (g, sc, C) in enumerate(zip(geoms, scenes, Cs)):
+            c, st = pool[i % lanes], streams[i % lanes]
+            with torch.cuda.stream(st):
+                bs.append(D.das_map(c, g, sc.freq, C, stream=st))
+                if compressed:
+                    sel.append(D.wavelet_compress_grid(c, bs[-1], sc.grid.nx, sc.grid.ny, LEVELS, D.PRED_HAAR,
+                                                       D.EPS_KEEP_FRAC, KEEP, stream=st))
+        fan_in()
         if compressed:
-            sel = [D.wavelet_compress_grid(ctx, b, sc.grid.nx, sc.grid.ny, LEVELS, D.PRED_HAAR, D.EPS_KEEP_FRAC, KEEP)
-                   for b, sc in zip(bs, scenes)]
             ns = torch.stack([n_t.reshape(()) for _, n_t, _, _ in sel]).tolist()   # one host read for all bins
+        fan_out()
         for i, (g, sc, b) in enumerate(zip(geoms, scenes, bs)):
-            if compressed:
-                n = int(ns[i])
-                idx = sel[i][0][:n]
-                b_sub = D.damas_gather(ctx, b, idx, n)
-            else:
-                n, idx, b_sub = S, None, b
-            A, g2 = D.damas_build_psf(ctx, g, sc.freq, idx, n)
-            x = torch.empty(n, dtype=torch.float32, device=dev)
+            c, st = pool[i % lanes], streams[i % lanes]
+            with torch.cuda.stream(st):
+                if compressed:
+                    n = int(ns[i])
+                    idx = sel[i][0][:n]
+                    b_sub = D.damas_gather(c, b, idx, n, stream=st)
+                else:
+                    n, idx, b_sub = S, None, b
+                A, g2 = D.damas_build_psf(c, g, sc.freq, idx, n, stream=st)
+                x = torch.empty(n, dtype=torch.float32, device=dev)
             systems.append(D.System(A, b_sub, x, ITERS))
             post.append((x, idx, g2, n))
+        fan_in()
         D.damas_solve(ctx, systems, status=status)
         return [D.damas_scatter_power(ctx, x, idx, g2, n, S) for x, idx, g2, n in post]
 
@@ -181,6 +207,9 @@ def batched_leg(ctx, D, dev, K: int, reps: int = 3):
         ms = statistics.median(ts)
         out[name] = {"ms_per_launch": round(ms, 2), "bins_per_s": round(K / (ms / 1e3), 1)}
         torch.cuda.empty_cache()
+    for c in pool[1:]:
+        c.close()
+    out["streams"] = lanes
     return out
 
 
