@@ -31,8 +31,10 @@
 // TMEM holds two accumulator slots (a = tile parity, 2 x 256 = 512 columns), so
 // the epilogue of one tile runs while the MMAs of the next fill the other slot.
 // The epilogue writes 32 x 32 blocks: the mirrored A[s][n] directly (the lanes
-// hold 32 consecutive n), the direct A[n][s] after a transpose through a
-// per-warp shared buffer, both as 128-byte warp stores.  For symmetric A (L and
+// hold 32 consecutive n, 128-byte warp stores); the direct A[n][s] (FP32) as one
+// TMA store of a per-warp staging tile in the tensor map's 128-byte swizzle,
+// while the warp goes on with the mirrored block (BF16: through a transpose
+// buffer and 128-byte warp stores).  For symmetric A (L and
 // R the same vectors, formulation E) only tiles that reach the upper triangle
 // run, every value with s >= n is also written mirrored, and A is exactly
 // symmetric.  Every wait is bounded by the global timer; a wait that runs out
@@ -47,6 +49,7 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -227,7 +230,20 @@ __device__ __forceinline__ void tile_coords(int t, int ntx, int symmetric, int &
 
 struct GramMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;  // boxes of 32 values x 128 rows, 128-byte swizzle
+    CUtensorMap out;                     // A (FP32 output only): boxes of 32 x 32, 128-byte swizzle
 };
+
+// 2-D TMA store of one 32 x 32 box from shared memory (bulk group of this thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <typename OutT>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -366,7 +382,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else {
         constexpr int CB = BN / 32 / 2;            // column blocks per warp
         const int q = warp & 3, half = warp >> 2;  // TMEM lane quarter, half of the column blocks
-        float *tp = tp_all + warp * 32 * 32;       // element (r, c) at r * 32 + (c ^ r)
+        // per-warp 32 x 32 buffer: the TMA staging tile of an FP32 output block, or
+        // (BF16 output) a transpose buffer with element (r, c) at r * 32 + (c ^ r)
+        float *tp = tp_all + warp * 32 * 32;
         const float nanv = __int_as_float(0x7fc00000);
         uint32_t k = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
@@ -406,16 +424,32 @@ __global__ void __launch_bounds__(THREADS, 1)
                         for (int j = 0; j < 32; ++j, p += lda)
                             if (j < jmax) put<OutT>(p, v[j]);
                     }
-                    // direct block A[n][sb..sb+31] through the transpose buffer
+                    if constexpr (std::is_same<OutT, float>::value) {
+                        // direct block A[n][sb..sb+31]: this lane's row into the staging
+                        // tile (128-byte swizzle: 16-byte chunk c of row r at c ^ (r mod 8)),
+                        // then one TMA store; rows past S are clipped by the tensor map.
+                        // The previous store of this warp must have read the tile.
+                        if (lane == 0) bulk_wait_read();
+                        __syncwarp();
+                        float4 *row = reinterpret_cast<float4 *>(tp + lane * 32);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) tp[lane * 32 + (j ^ lane)] = v[j];
-                    __syncwarp();
-                    const int imax = S - nb < 32 ? S - nb : 32;
-                    OutT *p = A + (size_t)nb * lda + sb + lane;
+                        for (int c4 = 0; c4 < 8; ++c4)
+                            row[c4 ^ (lane & 7)] = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+                        fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0 && nb < S) tma_store_2d(&maps.out, smem_u32(tp), sb, nb);
+                    } else {
+                        // direct block A[n][sb..sb+31] through the transpose buffer
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) tp[lane * 32 + (j ^ lane)] = v[j];
+                        __syncwarp();
+                        const int imax = S - nb < 32 ? S - nb : 32;
+                        OutT *p = A + (size_t)nb * lda + sb + lane;
 #pragma unroll 8
-                    for (int i = 0; i < 32; ++i, p += lda)
-                        if (i < imax) put<OutT>(p, tp[i * 32 + (lane ^ i)]);
-                    __syncwarp();
+                        for (int i = 0; i < 32; ++i, p += lda)
+                            if (i < imax) put<OutT>(p, tp[i * 32 + (lane ^ i)]);
+                        __syncwarp();
+                    }
                 } else {
                     // diagonal block: unit diagonal; symmetric A takes every pair
                     // from the value computed for s >= n
@@ -431,6 +465,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             fence_before();
             mbar_arrive(smem_u32(&acc_empty[a]));
         }
+        if (std::is_same<OutT, float>::value && lane == 0) bulk_wait_all();  // staging tile read and written out
+        __syncwarp();
         if (threadIdx.x == 0 && abort_flag) atomicAdd(&psf_timeouts, 1u);
     }
     fence_before();
@@ -462,6 +498,20 @@ EncodeTiledFn encode_fn() {
 
 // Tensor map over an operand plane (S rows of 2 ldm floats): boxes of 32
 // values x 128 rows with 128-byte swizzle; rows past S read as zeros.
+// Tensor map over the FP32 output A (S rows of lda values): boxes of 32 x 32,
+// 128-byte swizzle (the staging tiles' layout).
+bool make_out_map(CUtensorMap *m, float *A, int lda, int S) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)lda, (cuuint64_t)S};
+    const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(float)};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, A, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 bool make_map(CUtensorMap *m, const float *plane, int ldm, int S) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
@@ -498,6 +548,8 @@ cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre
     if (!make_map(&maps.a_hi, LH, ldm, S) || !make_map(&maps.a_lo, LL, ldm, S) || !make_map(&maps.b_hi, RH, ldm, S) ||
         !make_map(&maps.b_lo, RL, ldm, S))
         return cudaErrorInvalidValue;
+    memset(&maps.out, 0, sizeof(maps.out));
+    if (a_dtype != DAMAS_BF16 && !make_out_map(&maps.out, (float *)A, lda, S)) return cudaErrorInvalidValue;
 
     const int ntx = (lda + BN - 1) / BN, nty = (S + BM - 1) / BM;
     long long ntiles = 0;
