@@ -227,7 +227,7 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     S = sc.grid.S
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    launches_per_step = 8  # steer+das, wavelet, gather, steer+psf, sweep, scatter
+    launches_per_step = 9  # steer + das, wavelet, gather, steer + split + Gram, sweep, scatter
 
     def compressed_step(C, sweep_ev=None):
         b = D.das_map(ctx, geom, sc.freq, C)
