@@ -397,6 +397,26 @@ def test_batched_systems_equal_solo(ctx):
         assert torch.equal(a.x, s.x)
 
 
+def test_many_systems_one_call(ctx):
+    """40 systems of different sizes in one call (more than one launch used to hold):
+    each equals its solo solve bit for bit and matches the oracle iteration."""
+    rng = np.random.default_rng(31)
+    made = [synth.random_psd_system(rng, int(S)) for S in rng.integers(40, 200, size=40)]
+    systems, solo = [], []
+    for A64, b64 in made:
+        A = padded(A64)
+        b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+        systems.append(D.System(A, b, torch.zeros(len(b64), device="cuda"), 80))
+        solo.append(D.System(A, b, torch.zeros(len(b64), device="cuda"), 80))
+    D.damas_solve(ctx, systems)
+    for s_ in solo:
+        D.damas_solve(ctx, s_)
+    for (A64, b64), a, s_ in zip(made, systems, solo):
+        assert torch.equal(a.x, s_.x)
+    for q in (0, 17, 39):
+        assert rel_l2(systems[q].x.cpu().numpy(), _oracle_fp32_inputs(*made[q], 80)) <= 1e-4
+
+
 def test_large_batch_streamed_equals_solo(ctx):
     """A batch whose resident teams would need more than one launch is streamed so
     that all teams run side by side; every system still equals its solo solve (held
