@@ -30,11 +30,11 @@
 //                          writes |G|^2                         -> acc_empty[a]
 // TMEM holds two accumulator slots (a = tile parity, 2 x 256 = 512 columns), so
 // the epilogue of one tile runs while the MMAs of the next fill the other slot.
-// The epilogue writes 32 x 32 blocks: the mirrored A[s][n] directly (the lanes
-// hold 32 consecutive n, 128-byte warp stores); the direct A[n][s] (FP32) as one
-// TMA store of a per-warp staging tile in the tensor map's 128-byte swizzle,
-// while the warp goes on with the mirrored block (BF16: through a transpose
-// buffer and 128-byte warp stores).  For symmetric A (L and
+// The epilogue writes 32 x 32 blocks.  FP32: the direct block A[n][s] and then
+// its mirror A[s][n] as TMA stores of one per-warp staging tile in the tensor
+// map's 128-byte swizzle (rows, then columns, of the lanes' values).  BF16: the
+// mirror as 128-byte warp stores (lanes hold 32 consecutive n) and the direct
+// block through a transpose buffer.  For symmetric A (L and
 // R the same vectors, formulation E) only tiles that reach the upper triangle
 // run, every value with s >= n is also written mirrored, and A is exactly
 // symmetric.  Every wait is bounded by the global timer; a wait that runs out
@@ -416,19 +416,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 // columns >= S come out as exact zeros (their operands are zero)
                 if (sb != nb) {
-                    if (symmetric) {
-                        // mirrored block A[s][n], s = sb + j: lanes cover 32 consecutive n
-                        OutT *p = A + (size_t)sb * lda + n;
-                        const int jmax = S - sb < 32 ? S - sb : 32;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j, p += lda)
-                            if (j < jmax) put<OutT>(p, v[j]);
-                    }
                     if constexpr (std::is_same<OutT, float>::value) {
                         // direct block A[n][sb..sb+31]: this lane's row into the staging
                         // tile (128-byte swizzle: 16-byte chunk c of row r at c ^ (r mod 8)),
                         // then one TMA store; rows past S are clipped by the tensor map.
-                        // The previous store of this warp must have read the tile.
+                        // The warp's previous store must have read the tile first.
                         if (lane == 0) bulk_wait_read();
                         __syncwarp();
                         float4 *row = reinterpret_cast<float4 *>(tp + lane * 32);
@@ -438,7 +430,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                         fence_proxy_async();
                         __syncwarp();
                         if (lane == 0 && nb < S) tma_store_2d(&maps.out, smem_u32(tp), sb, nb);
+                        if (symmetric) {
+                            // mirrored block A[sb + j][nb + lane]: the same values transposed
+                            // into the tile (lane = column), once the direct store has read it
+                            if (lane == 0) bulk_wait_read();
+                            __syncwarp();
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) tp[j * 32 + ((((lane >> 2) ^ (j & 7))) << 2) + (lane & 3)] = v[j];
+                            fence_proxy_async();
+                            __syncwarp();
+                            if (lane == 0 && sb < S && nb < lda) tma_store_2d(&maps.out, smem_u32(tp), nb, sb);
+                        }
                     } else {
+                        if (symmetric) {
+                            // mirrored block A[s][n], s = sb + j: lanes cover 32 consecutive n
+                            OutT *p = A + (size_t)sb * lda + n;
+                            const int jmax = S - sb < 32 ? S - sb : 32;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j, p += lda)
+                                if (j < jmax) put<OutT>(p, v[j]);
+                        }
                         // direct block A[n][sb..sb+31] through the transpose buffer
 #pragma unroll
                         for (int j = 0; j < 32; ++j) tp[lane * 32 + (j ^ lane)] = v[j];
