@@ -488,7 +488,8 @@ def run_band(args):
         e1.record()
         bs.check()
         ms = e0.elapsed_time(e1) / args.steps
-        # the solve launch alone
+        replayed = [x.clone() for x in bs.x]
+        # the solve launch alone (it also re-checks the replayed results, bit for bit)
         systems = bs.systems()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
@@ -496,6 +497,8 @@ def run_band(args):
         s1.record()
         bs.check()
         solve_ms = s0.elapsed_time(s1)
+        if not all(torch.equal(a, b) for a, b in zip(replayed, bs.x)):
+            raise RuntimeError("band: graph replay and direct solve differ")
         bytes_ = sum(float(n) * n for n in grids.S_f) * elt * 1000
         out[name] = {"bins_per_s": round(64 / (ms / 1e3), 2), "ms_per_band": round(ms, 2), "solve_ms": round(solve_ms, 2),
                      "sweep_gbs": round(bytes_ / (solve_ms / 1e3) / 1e9, 1), "ctas": sum(bs.ctas),

@@ -18,6 +18,11 @@
  *  - A context owns scratch device memory (grown on demand, outside any
  *    captured region) that calls on that context share: issue the calls of one
  *    context on one stream, or serialise them.
+ *  - Calls may be recorded into a CUDA graph (stream capture) once an eager run
+ *    of the same calls has sized the scratch.  A recorded damas_solve clears its
+ *    exchange words at the start of every replay, so a graph can be replayed any
+ *    number of times, between eager calls on the same context; a later call that
+ *    needs more scratch reallocates it and the graph must be recorded again.
  *  - Scan grid (§2): nx x ny points at (x0 + ix*dx, y0 + iy*dy, z), index
  *    n = iy*nx + ix; the array centre is the origin.
  *  - Equation numbers follow the order of the paper's displayed equations:

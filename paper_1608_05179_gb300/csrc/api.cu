@@ -525,10 +525,21 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     int *status = cfg && cfg->status_dev ? cfg->status_dev : (int *)ctx->status.ptr;
     DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
 
+    // A launch recorded into a CUDA graph keeps the epoch it was recorded with, so
+    // every replay would find the words of the previous replay already "new": the
+    // recording clears the mailbox words first, and each replay starts from zero.
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    DAMAS_CUDA_TRY(ctx, cudaStreamIsCapturing(st, &cap_status));
+    const bool capturing = cap_status == cudaStreamCaptureStatusActive;
     for (const Launch &L : launches) {
         if ((unsigned long long)ctx->epoch + L.max_iters + 2 >= 0xffffffffull) {
             DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->solve.ptr, 0, ctx->solve.cap, st));
             ctx->epoch = 0;
+        }
+        if (capturing) {
+            size_t used = 0;
+            for (int i : L.ids) used += (size_t)((sys[i].S + 31) / 32) * 32 * sizeof(unsigned long long);
+            DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->solve.ptr, 0, used, st));
         }
         SweepParams p;
         memset(&p, 0, sizeof(p));

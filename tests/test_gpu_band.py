@@ -48,12 +48,17 @@ def test_batched_equals_solo_and_graph_replay(ctx):
         solo = torch.zeros_like(bs.x[f])
         D.damas_solve(ctx, D.System(bs.A[f], bs.b_sub[f], solo, 60))
         assert torch.equal(solo, x_batch[f]), f
-    # graph replay of phase 2
+    # graph replay of phase 2, several times (each replay starts from clean mailboxes),
+    # with an eager solve on the same context in between
     bs.capture(grids)
-    bs.replay()
-    bs.check()
-    for f in range(len(freqs)):
-        assert torch.equal(bs.x[f], x_batch[f]), f
+    for rep in range(3):
+        bs.replay()
+        bs.check()
+        for f in range(len(freqs)):
+            assert torch.equal(bs.x[f], x_batch[f]), (rep, f)
+        solo = torch.zeros_like(bs.x[0])
+        D.damas_solve(ctx, D.System(bs.A[0], bs.b_sub[0], solo, 60))
+        assert torch.equal(solo, x_batch[0])
 
 
 def test_batched_solve_matches_oracle(ctx):
