@@ -389,7 +389,11 @@ def _handover_floor(D, ctx, S_sub, S, sweep_c_ms, sweep_f_ms):
         floor = ITERS * (ncta if ncta > 1 else 0) * med / 1e6
         out[name] = {"team_ctas": ncta, "rows_per_cta": rows, "blocks_per_sweep": -(-n // 32),
                      "handovers_per_sweep": ncta if ncta > 1 else 0, "floor_ms": round(floor, 3),
-                     "launch_ms": round(ms, 3), "frac": round(floor / ms, 3)}
+                     "launch_ms": round(ms, 3), "frac": round(floor / ms, 3),
+                     "step_ns": round(ms * 1e6 / (ITERS * -(-n // 32)), 1)}
+        if ncta == 1:
+            out[name]["form"] = "single CTA: no hand-overs; each 32-row step is the row chain and one CTA barrier"
+
     return out
 
 

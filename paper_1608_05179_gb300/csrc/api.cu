@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
@@ -324,11 +325,20 @@ int damas_scatter_power(damas_ctx *ctx, const float *x_sub_dev, const int32_t *i
 namespace {
 
 struct Plan {
-    int ncta, R, resident;
+    int ncta, R, resident, solo;
     size_t smem;
 };
 
-Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int placement, int cta_budget) {
+// Systems up to this many rows run the single-CTA form when no team size is asked
+// for: on such systems its step (the row chain and one barrier) is no longer than
+// a team's average step with its hand-overs between CTAs (FP32 A, 1000 sweeps:
+// 11.9 / 17.4 / 25.8 ms at S = 441 / 657 / 985 against 12.8 / 18.3 / 26.2 ms for
+// the best team; 37.8 against 34.0 ms at S = 1313), and a batch of them needs no
+// co-residency.
+constexpr int SOLO_AUTO_ROWS = 1024;
+
+Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int placement, int cta_budget,
+                 bool allow_solo = true) {
     const int nb = (s.S + 31) / 32;
     const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
     Plan p{};
@@ -344,6 +354,17 @@ Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int pl
     const int rmax_res = (int)std::min<size_t>(budget / per_row, (size_t)1 << 20) / 32 * 32;
     if (nb == 1) {  // a single block is always held in shared memory
         finish(32, true);
+        return p;
+    }
+    // one CTA without hand-overs (asked for, or by default for small systems)
+    const size_t solo_smem = sweep_solo_smem_bytes(nb * 32, s.a_dtype);
+    if (allow_solo && nb >= 4 && placement != 1 && solo_smem <= budget &&
+        (forced == 1 || (forced == 0 && s.S <= SOLO_AUTO_ROWS))) {
+        p.ncta = 1;
+        p.R = nb * 32;
+        p.resident = 0;
+        p.solo = 1;
+        p.smem = solo_smem;
         return p;
     }
     if (forced > 0) {
@@ -438,6 +459,19 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     std::vector<Plan> plans(nsys);
     for (int i = 0; i < nsys; ++i)
         plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement, ctx->sm_count);
+    {
+        // The single-CTA form runs in a launch of its own.  A call that also holds
+        // teams keeps every system in the teams' one launch (launches on a stream
+        // run one after another), so there the single-CTA systems become one-CTA
+        // teams.
+        int nsolo = 0;
+        for (const Plan &q : plans) nsolo += q.solo;
+        if (nsolo > 0 && nsolo < nsys)
+            for (int i = 0; i < nsys; ++i)
+                if (plans[i].solo)
+                    plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement,
+                                           ctx->sm_count, false);
+    }
     if (placement == 0 && nsys > 1) {
         // A batch whose resident teams need more than one launch (a resident CTA
         // fills an SM) but whose streamed teams fit in one (two CTAs per SM) is
@@ -460,7 +494,8 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
             std::vector<Plan> streamed(nsys);
             for (int i = 0; i < nsys; ++i)
                 streamed[i] = plans[i].resident
-                                  ? plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, 2, ctx->sm_count)
+                                  ? plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, 2, ctx->sm_count,
+                                                false)
                                   : plans[i];
             if (fits_once(streamed)) plans.swap(streamed);
         }
@@ -470,6 +505,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         if (plans[i].smem > ctx->smem_optin - 1024)
             return ctx_fail(ctx, DAMAS_EINVAL, "system %d: %zu bytes of shared memory per CTA do not fit", i,
                             plans[i].smem);
+        if (plans[i].solo) continue;
         int occ = 0;
         cudaError_t e = sweep_occupancy(plans[i].smem, &occ);
         if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
@@ -482,21 +518,27 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         size_t smem = 0;
         int ctas = 0;
         int max_iters = 0;
+        int solo = 0;
     };
     std::vector<Launch> launches;
     {
+        // a launch holds either single-CTA systems (any number of CTAs: none waits
+        // on another) or teams (all co-resident)
         Launch cur;
         for (int i = 0; i < nsys; ++i) {
             const Plan &pl = plans[i];
-            const size_t smem = std::max(cur.smem, pl.smem);
-            int occ = 0;
-            cudaError_t e = sweep_occupancy(smem, &occ);
-            if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-            const int cap = occ * ctx->sm_count;
-            if (!cur.ids.empty() && ((int)cur.ids.size() == SWEEP_MAX_SYS || cur.ctas + pl.ncta > cap)) {
+            bool flush = !cur.ids.empty() && ((int)cur.ids.size() == SWEEP_MAX_SYS || cur.solo != pl.solo);
+            if (!flush && !pl.solo && !cur.ids.empty()) {
+                int occ = 0;
+                cudaError_t e = sweep_occupancy(std::max(cur.smem, pl.smem), &occ);
+                if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+                flush = cur.ctas + pl.ncta > occ * ctx->sm_count;
+            }
+            if (flush) {
                 launches.push_back(cur);
                 cur = Launch();
             }
+            cur.solo = pl.solo;
             cur.ids.push_back(i);
             cur.smem = std::max(cur.smem, pl.smem);
             cur.ctas += pl.ncta;
@@ -574,7 +616,15 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
             d.epoch0 = ctx->epoch;
             cta += pl.ncta;
         }
-        DAMAS_CUDA_TRY(ctx, launch_sweep(p, cta, L.smem, st));
+        if (L.solo) {
+            std::unique_ptr<SoloMaps> maps(new SoloMaps());  // copied into the launch's parameters
+            for (int q = 0; q < p.nsys; ++q)
+                if (!make_sweep_tile_map(&maps->m[q], p.sys[q].At, p.sys[q].dtype, p.sys[q].lda, p.sys[q].S))
+                    return ctx_fail(ctx, DAMAS_ECUDA, "tensor map for system %d", L.ids[q]);
+            DAMAS_CUDA_TRY(ctx, launch_sweep_solo(p, *maps, L.smem, st));
+        } else {
+            DAMAS_CUDA_TRY(ctx, launch_sweep(p, cta, L.smem, st));
+        }
         ctx->epoch += (unsigned)L.max_iters + 1u;
     }
     if (cfg && cfg->status_dev) return DAMAS_OK;

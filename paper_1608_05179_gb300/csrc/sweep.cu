@@ -799,6 +799,495 @@ __global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepP
     }
 }
 
+// ---------------------------------------------------------------- single-CTA form
+// One CTA per system, A streamed from global memory: every block is the CTA's
+// own, so there are no hand-overs and a step is the row chain plus one CTA
+// barrier.  The rest of the step's work is arranged so that it finishes within
+// the chain:
+//  - one thread of warp 4 keeps a ring of tile slots filled SOLO_PD steps ahead
+//    by TMA (four 32x32 boxes of At per step, completion counted on the slot's
+//    mbarrier): the chain and partial tiles of block J for warp 0, and the tiles
+//    of columns J-2 and J-1 over the rows of block J+1;
+//  - the helper warp (1) folds dx_{G-2} and then dx_{G-1} into the rows of
+//    block J+1 from those tiles, so that block is current through dx_{G-1} when
+//    warp 0 solves it in step G+1 (adding dx_G itself, as in the team form);
+//  - the updater warps (all but 0, 1, 4, 8 and 12) issue, in step G,
+//    asynchronous copies of the entries of A that dx_{G-1} needs for their own
+//    rows (the first SOLO_STAGE nonzero columns) into a staging buffer, and fold
+//    dx_{G-2} from the buffer filled in step G-1 into every row but those of
+//    blocks J and J+1: the loads of a fold are in flight for a whole step.
+//    The last of them also forms the bound of block J-1 from that block's
+//    diagonal tile (its own rows start at 1280, so it is otherwise idle on
+//    compressed grids);
+//  - warps 8 and 12 share warp 0's scheduler and only join the barriers.
+// Every row still receives every dx in step order through the same error-free
+// fold arithmetic, and warp 0 solves from the same residual and partial, so the
+// iterates are bit for bit those of the team form; so are the state written at
+// the end and the state a call starts from.
+constexpr int SOLO_SLOTS = 6;          // tile slots; the slot of step G+SOLO_PD is refilled in step G
+constexpr int SOLO_PD = 4;             // (slots G-1 and G are read in step G: SOLO_SLOTS >= SOLO_PD + 2)
+constexpr int SOLO_STAGE = 8;          // staged columns per dx (further nonzero columns are read directly)
+constexpr int SOLO_THREADS = 512;      // 16 warps
+constexpr int SOLO_UPD_THREADS = 352;  // the updaters: every warp but 0, 1, 4, 8 and 12
+static_assert(SOLO_SLOTS >= SOLO_PD + 2, "a slot must not be refilled while it is read");
+
+__device__ __forceinline__ bool solo_updater(int warp) { return warp >= 2 && (warp & 3) != 0; }
+__device__ __forceinline__ int solo_upd_index(int warp) { return warp - 2 - (warp >> 2); }
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void solo_mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void solo_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool solo_mbar_wait(uint32_t bar, uint32_t parity, unsigned long long timeout_ns) {
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((i & 15u) == 15u) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            if (now - t0 > timeout_ns) return false;
+        }
+    }
+}
+// One 32 x 32 box of At (x = column, y = row; rows past S read as zeros).
+__device__ __forceinline__ void solo_tma_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Helper warp, one thread: the four tiles of step G (block J) into one slot,
+// tile(Y, X)[j][k] = At[32X + j][32Y + k]: (J, J) the chain, (J, J-1) warp 0's
+// partial, (J+1, J-2) and (J+1, J-1) the helper's fold into block J+1.
+__device__ __forceinline__ void solo_issue_tiles(const CUtensorMap *map, const Team &T, char *slot, uint32_t bar,
+                                                 int J) {
+    const int nb = T.nb;
+    const int Jp1 = J + 1 == nb ? 0 : J + 1;
+    const int Jm1 = J == 0 ? nb - 1 : J - 1;
+    const int Jm2 = Jm1 == 0 ? nb - 1 : Jm1 - 1;
+    const int tile_bytes = 32 * T.tile_ld;
+    solo_expect_tx(bar, 4u * tile_bytes);
+    solo_tma_box(smem_addr(slot), map, 32 * J, 32 * J, bar);
+    solo_tma_box(smem_addr(slot + tile_bytes), map, 32 * J, 32 * Jm1, bar);
+    solo_tma_box(smem_addr(slot + 2 * tile_bytes), map, 32 * Jp1, 32 * Jm2, bar);
+    solo_tma_box(smem_addr(slot + 3 * tile_bytes), map, 32 * Jp1, 32 * Jm1, bar);
+}
+
+// Helper warp: fold dx list 2 (tile t2) and then dx list 1 (tile t1) into the
+// rows of block Y (lane = row).  Each list's sum is formed exactly as by
+// dot_list; the lists are short (a few nonzero dx per block), so they are walked
+// two columns at a time, both lists together.
+template <bool F32>
+__device__ __forceinline__ void solo_tile_fold2(const Team &T, const char *t2, const char *t1, int Y, const float *d2,
+                                                const unsigned char *idx2, int n2, const float *d1,
+                                                const unsigned char *idx1, int n1, float *rh, float *rl) {
+    const int k = threadIdx.x & 31, r = Y * 32 + k;
+    if ((n1 == 0 && n2 == 0) || r >= T.S) return;
+    float h2 = 0.f, l2 = 0.f, h1 = 0.f, l1 = 0.f;
+    const int n = n1 > n2 ? n1 : n2;
+    for (int q0 = 0; q0 < n; q0 += 2) {
+        int c2[2], c1[2];
+        float a2[2], a1[2], e2[2], e1[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            c2[u] = q0 + u < n2 ? idx2[q0 + u] : 0;
+            c1[u] = q0 + u < n1 ? idx1[q0 + u] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            e2[u] = d2[c2[u]];
+            a2[u] = tile_at<F32>(T, t2, c2[u], k);
+            e1[u] = d1[c1[u]];
+            a1[u] = tile_at<F32>(T, t1, c1[u], k);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float p, pe, t;
+            if (q0 + u < n2) {
+                two_prod(a2[u], e2[u], p, pe);
+                two_sum(h2, p, h2, t);
+                l2 = __fadd_rn(l2, __fadd_rn(t, pe));
+            }
+            if (q0 + u < n1) {
+                two_prod(a1[u], e1[u], p, pe);
+                two_sum(h1, p, h1, t);
+                l1 = __fadd_rn(l1, __fadd_rn(t, pe));
+            }
+        }
+    }
+    if (n2) fold(rh, rl, r, h2, l2);
+    if (n1) fold(rh, rl, r, h1, l1);
+}
+
+// One warp: block_bound of block Jb from its diagonal tile (Jb, Jb).
+template <bool F32>
+__device__ __forceinline__ void solo_tile_bound(const Team &T, const char *tdiag, int Jb, const float *xs,
+                                                float *bnd) {
+    const int k = threadIdx.x & 31, r = Jb * 32 + k;
+    const bool valid = r < T.S;
+    const float xk = valid ? xs[r] : 0.f;
+    unsigned m = __ballot_sync(FULL, xk > 0.f);
+    float b = 0.f;
+    while (m) {
+        int c[8], cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            c[q] = m ? __ffs(m) - 1 : 0;
+            if (m) {
+                m &= m - 1u;
+                ++cnt;
+            }
+        }
+        float a[8], xj[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            xj[q] = __shfl_sync(FULL, xk, c[q]);
+            a[q] = q < cnt ? tile_at<F32>(T, tdiag, c[q], k) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < cnt && c[q] < k) b = __fmaf_rn(a[q], xj[q], b);
+    }
+    if (valid) bnd[r] = b;
+}
+
+// Updater thread ut: copy At[c0 + idx[u]][4g .. 4g+3] for its groups g of four
+// rows (blocks e1 and e2 left out) and the first SOLO_STAGE listed columns into
+// stage[u][4g ..]; always commits one group.
+template <bool F32>
+__device__ __forceinline__ void solo_stage(const SweepSys &s, const Team &T, char *stage, int ut, int c0,
+                                           const unsigned char *idx, int n, int e1, int e2) {
+    const int ns = n < SOLO_STAGE ? n : SOLO_STAGE;
+    const int elt = F32 ? 4 : 2;
+    const size_t col_bytes = (size_t)T.R * elt;
+    if (ns > 0)
+        for (int g = ut; 4 * g < T.S; g += SOLO_UPD_THREADS) {
+            const int blk = g >> 3;
+            if (blk == e1 || blk == e2) continue;
+            for (int u = 0; u < ns; ++u) {
+                const char *src = (const char *)s.At + ((size_t)(c0 + idx[u]) * s.lda + 4 * g) * elt;
+                char *dst = stage + u * col_bytes + (size_t)4 * g * elt;
+                if (F32)
+                    cp_async16(dst, src);
+                else
+                    cp_async8(dst, src);
+            }
+        }
+    cp_async_commit();
+}
+
+// Updater thread ut: fold the listed dx (columns c0 + idx[u]) into the rows of
+// its groups: every block but skip1 and skip2, or only block `only` when it is
+// >= 0.  Entries come from `stage` (filled by solo_stage with blocks nost1 and
+// nost2 left out) for the first SOLO_STAGE columns, else from global memory.
+// Each row's sum is formed exactly as by dot_list.
+template <bool F32>
+__device__ __forceinline__ void solo_consume(const SweepSys &s, const Team &T, const char *stage, int ut, int c0,
+                                             const float *d, const unsigned char *idx, int n, int skip1, int skip2,
+                                             int only, int nost1, int nost2, float *rh, float *rl) {
+    if (n == 0) return;
+    const int elt = F32 ? 4 : 2;
+    const size_t col_bytes = (size_t)T.R * elt;
+    for (int g = ut; 4 * g < T.S; g += SOLO_UPD_THREADS) {
+        const int blk = g >> 3;
+        if (only >= 0 ? blk != only : (blk == skip1 || blk == skip2)) continue;
+        const bool staged = stage != nullptr && blk != nost1 && blk != nost2;
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int u0 = 0; u0 < n; u0 += 2) {  // two columns at a time, their loads together
+            float a[2][4], dd[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int u = u0 + v < n ? u0 + v : u0;
+                const int c = idx[u];
+                dd[v] = d[c];
+                if (staged && u < SOLO_STAGE) {
+                    const char *p = stage + u * col_bytes + (size_t)4 * g * elt;
+                    if (F32) {
+                        const float4 w = *(const float4 *)p;
+                        a[v][0] = w.x;
+                        a[v][1] = w.y;
+                        a[v][2] = w.z;
+                        a[v][3] = w.w;
+                    } else {
+                        const uint2 w = *(const uint2 *)p;
+                        a[v][0] = bf16_lo(w.x);
+                        a[v][1] = bf16_hi(w.x);
+                        a[v][2] = bf16_lo(w.y);
+                        a[v][3] = bf16_hi(w.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) a[v][q] = col_at<F32>(s, c0 + c, 4 * g + q);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 2; ++v)
+                if (u0 + v < n) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float p, pe, t;
+                        two_prod(a[v][q], dd[v], p, pe);
+                        two_sum(hi[q], p, hi[q], t);
+                        lo[q] = __fadd_rn(lo[q], __fadd_rn(t, pe));
+                    }
+                }
+        }
+        // fold() on the four rows, as one 16-byte access to each half of the pair
+        float4 *ph = (float4 *)(rh + 4 * g), *pl = (float4 *)(rl + 4 * g);
+        float4 h4 = *ph, l4 = *pl;
+        float hh[4] = {h4.x, h4.y, h4.z, h4.w}, ll[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * g + q < T.S) {
+                float h, t;
+                two_sum(hh[q], hi[q], h, t);
+                hh[q] = h;
+                ll[q] = __fadd_rn(ll[q], __fadd_rn(lo[q], t));
+            }
+        *ph = make_float4(hh[0], hh[1], hh[2], hh[3]);
+        *pl = make_float4(ll[0], ll[1], ll[2], ll[3]);
+    }
+}
+
+template <bool F32>
+__device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys &s, const CUtensorMap *map,
+                                           float (*dring)[32], unsigned char (*nzidx)[32], int *nzcnt,
+                                           unsigned long long *tbar, int *s_abort_p, char *smem) {
+    int &s_abort = *s_abort_p;
+    Team T;
+    T.S = s.S;
+    T.nb = (s.S + 31) / 32;
+    T.R = T.nb * 32;
+    T.row0 = 0;
+    T.nrows = s.S;
+    T.jb0 = 0;
+    T.jb1 = T.nb;
+    T.lds_w = 0;
+    T.tile_ld = 32 * (F32 ? 4 : 2);  // dense 32 x 32 boxes as TMA writes them
+    const int S = T.S, nb = T.nb, R = T.R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long Gend = (long long)s.iters * nb;
+    const int elt = F32 ? 4 : 2;
+    const bool upd = solo_updater(warp);
+    const int ut = upd ? solo_upd_index(warp) * 32 + lane : 0;
+
+    // tile slots first, 128-byte aligned for TMA; then rows and staging
+    char *tiles = smem + ((128u - (smem_addr(smem) & 127u)) & 127u);
+    const int slot_bytes = 4 * 32 * T.tile_ld;
+    float *rh = (float *)(tiles + SOLO_SLOTS * slot_bytes);
+    float *rl = rh + R;
+    float *xs = rl + R;
+    float *bnd = xs + R;
+    char *stage = (char *)(bnd + R);
+    const size_t stage_bytes = (size_t)SOLO_STAGE * R * elt;
+
+    // ---- prologue (as in the team form)
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < SOLO_SLOTS; ++q) solo_mbar_init(smem_addr(&tbar[q]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    for (int r = threadIdx.x; r < R; r += SOLO_THREADS) {
+        const bool ok = r < S;
+        xs[r] = (ok && s.init != DAMAS_INIT_ZERO) ? s.x[r] : 0.f;
+        rh[r] = ok ? (s.init == DAMAS_INIT_STATE ? s.state[r] : (s.init == DAMAS_INIT_X ? 0.f : -s.b[r])) : 0.f;
+        rl[r] = (ok && s.init == DAMAS_INIT_STATE) ? s.state[S + r] : 0.f;
+        bnd[r] = 0.f;
+    }
+    if (warp == 0) {
+        const bool have = s.init == DAMAS_INIT_STATE;
+        for (int q = 0; q < 4; ++q) {
+            const float d = (have && q >= 2) ? s.state[2 * S + (q - 2) * 32 + lane] : 0.f;
+            dring[q][lane] = d;
+            make_list(d, nzidx[q], &nzcnt[q]);
+        }
+    }
+    __syncthreads();
+    // tile slots of steps 0 .. SOLO_PD-1 (helper thread); phase bit q: parity of
+    // the next completion of slot q
+    uint32_t phase = 0;
+    if (warp == 4 && lane == 0)
+        for (int q = 0; q < SOLO_PD && q < Gend; ++q)
+            solo_issue_tiles(map, T, tiles + q * slot_bytes, smem_addr(&tbar[q]), q % nb);
+    if (s.init == DAMAS_INIT_X) {
+        for (int r = warp; r < S; r += SOLO_THREADS / 32) {
+            float hi = 0.f, lo = 0.f;
+            const char *Arow = (const char *)s.A + (size_t)r * s.lda * elt;
+            for (int j = lane; j < S; j += 32) {
+                const float a = F32 ? ((const float *)Arow)[j] : bf16_bits(((const unsigned short *)Arow)[j]);
+                float pr, pe, t;
+                two_prod(a, s.x[j], pr, pe);
+                two_sum(hi, pr, hi, t);
+                lo = __fadd_rn(lo, __fadd_rn(t, pe));
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const float h2 = __shfl_xor_sync(FULL, hi, o), l2 = __shfl_xor_sync(FULL, lo, o);
+                float t;
+                two_sum(hi, h2, hi, t);
+                lo = __fadd_rn(__fadd_rn(lo, l2), t);
+            }
+            if (lane == 0) {
+                float h, t;
+                two_sum(hi, -s.b[r], h, t);
+                rh[r] = h;
+                rl[r] = __fadd_rn(lo, t);
+            }
+        }
+    }
+    bool nonneg_all;
+    {
+        int negs = 0;
+        const char *gA = (const char *)s.A;
+        for (int e = threadIdx.x; e < S * 32; e += SOLO_THREADS) {
+            const int r = e >> 5, c = r / 32 * 32 + (e & 31);
+            if (c < S) {
+                const size_t o = (size_t)r * s.lda + c;
+                const float a = F32 ? ((const float *)gA)[o] : bf16_bits(((const unsigned short *)gA)[o]);
+                negs |= a < 0.f;
+            }
+        }
+        nonneg_all = !__syncthreads_or(negs);
+    }
+    for (int Jb = warp; Jb < nb; Jb += SOLO_THREADS / 32) block_bound<F32, false>(s, T, nullptr, Jb, xs, bnd);
+    if (warp == 4 && lane == 0 && Gend > 0) {
+        if (solo_mbar_wait(smem_addr(&tbar[0]), 0, p.timeout_ns)) {
+            phase ^= 1u;
+        } else {
+            atomicCAS(p.status, 0, DAMAS_ETIMEDOUT);
+            s_abort = 1;
+        }
+    }
+    __syncthreads();
+
+    // ---- steps
+    float dprev = dring[3][lane];
+    int J = 0, sl = 0, slm1 = SOLO_SLOTS - 1, pf_sl = SOLO_PD % SOLO_SLOTS, pf_J = SOLO_PD % nb;
+    long long G = 0;
+    for (; G < Gend && !s_abort; ++G) {
+        const int Jm1 = J == 0 ? nb - 1 : J - 1;
+        const int Jm2 = Jm1 == 0 ? nb - 1 : Jm1 - 1;
+        const int Jp1 = J + 1 == nb ? 0 : J + 1;
+        const int Jp2 = Jp1 + 1 == nb ? 0 : Jp1 + 1;
+        const int gi = (int)(G & 3), g1 = (gi + 3) & 3, g2 = (gi + 2) & 3;
+        const char *slot = tiles + sl * slot_bytes;
+        if (warp == 0) {
+            const float dk = solve_block2<F32, false>(T, nullptr, slot, J, Jm1, xs, rh, rl, bnd, dprev, true,
+                                                      nonneg_all);
+            dprev = dk;
+            dring[gi][lane] = dk;
+            make_list(dk, nzidx[gi], &nzcnt[gi]);
+        } else if (warp == 1) {
+            // block J+1: dx_{G-2} (which a call resumed from a state already folded
+            // there), then dx_{G-1}
+            const int tb = 32 * T.tile_ld;
+            solo_tile_fold2<F32>(T, slot + 2 * tb, slot + 3 * tb, Jp1, dring[g2], nzidx[g2], G > 0 ? nzcnt[g2] : 0,
+                                 dring[g1], nzidx[g1], nzcnt[g1], rh, rl);
+        } else if (warp == 4) {
+            // one thread: the tiles of step G+SOLO_PD, then the wait for those of step G+1
+            if (lane == 0 && G + SOLO_PD < Gend)
+                solo_issue_tiles(map, T, tiles + pf_sl * slot_bytes, smem_addr(&tbar[pf_sl]), pf_J);
+            if (lane == 0 && G + 1 < Gend) {
+                const int s1 = sl + 1 == SOLO_SLOTS ? 0 : sl + 1;
+                if (solo_mbar_wait(smem_addr(&tbar[s1]), (phase >> s1) & 1u, p.timeout_ns)) {
+                    phase ^= 1u << s1;
+                } else {
+                    atomicCAS(p.status, 0, DAMAS_ETIMEDOUT);
+                    s_abort = 1;
+                }
+            }
+        } else if (upd) {
+            solo_stage<F32>(s, T, stage + (G & 1) * stage_bytes, ut, Jm1 * 32, nzidx[g1], nzcnt[g1], Jp1, Jp2);
+            cp_async_wait_group<1>();  // the copies of step G-1
+            if (G == 0)  // a resumed state holds dx_{-2} everywhere but in block nb-1
+                solo_consume<F32>(s, T, nullptr, ut, Jm2 * 32, dring[g2], nzidx[g2], nzcnt[g2], -1, -1, Jm1, -1, -1, rh,
+                                  rl);
+            else
+                solo_consume<F32>(s, T, stage + ((G - 1) & 1) * stage_bytes, ut, Jm2 * 32, dring[g2], nzidx[g2],
+                                  nzcnt[g2], J, Jp1, -1, J, Jp1, rh, rl);
+            // the last updater warp (whose rows start at 1280): block J-1 was solved
+            // in the previous step, its bound for the next solve
+            if (warp == SOLO_THREADS / 32 - 1 && G > 0)
+                solo_tile_bound<F32>(T, tiles + slm1 * slot_bytes, Jm1, xs, bnd);
+        }
+        __syncthreads();
+        J = Jp1;
+        slm1 = sl;
+        sl = sl + 1 == SOLO_SLOTS ? 0 : sl + 1;
+        pf_sl = pf_sl + 1 == SOLO_SLOTS ? 0 : pf_sl + 1;
+        pf_J = pf_J + 1 == nb ? 0 : pf_J + 1;
+    }
+    if (s_abort) {
+        // a tile wait ran out (for step G): let the boxes still in flight, those of
+        // steps G .. G+SOLO_PD-1, land (bounded), then stop
+        if (warp == 4 && lane == 0)
+            for (long long q = G; q < G + SOLO_PD && q < Gend; ++q) {
+                const int sq = (int)(q % SOLO_SLOTS);
+                if (solo_mbar_wait(smem_addr(&tbar[sq]), (phase >> sq) & 1u, p.timeout_ns)) phase ^= 1u << sq;
+            }
+        cp_async_wait_all();
+        __syncthreads();
+        return;
+    }
+
+    // ---- drain to the team form's final state: dx_{Gend-2} into every block
+    // but 0 (the helper's) and nb-1 (which the team form also leaves without it)
+    if (Gend > 0 && upd) {
+        cp_async_wait_all();
+        const int gq = (int)((Gend - 2) & 3);
+        solo_consume<F32>(s, T, stage + ((Gend - 1) & 1) * stage_bytes, ut, (nb - 2) * 32, dring[gq], nzidx[gq],
+                          nzcnt[gq], 0, nb - 1, -1, 0, 1, rh, rl);
+    }
+    __syncthreads();
+
+    // ---- results: x, and the state a later call continues from
+    for (int r = threadIdx.x; r < S; r += SOLO_THREADS) {
+        s.x[r] = xs[r];
+        if (s.state) {
+            s.state[r] = rh[r];
+            s.state[S + r] = rl[r];
+        }
+    }
+    if (s.state && threadIdx.x < 64) {
+        const long long Gx = Gend - 2 + (threadIdx.x >> 5);
+        s.state[2 * S + threadIdx.x] = dring[Gx & 3][lane];
+    }
+    cp_async_wait_all();
+}
+
+__global__ void __launch_bounds__(SOLO_THREADS, 1)
+    damas_sweep_solo_kernel(const SweepParams p, const __grid_constant__ SoloMaps maps) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ float dring[4][32];
+    __shared__ unsigned char nzidx[4][32];
+    __shared__ int nzcnt[4];
+    __shared__ __align__(8) unsigned long long tbar[SOLO_SLOTS];
+    __shared__ int s_abort;
+    const SweepSys s = p.sys[blockIdx.x];
+    if (s.dtype == DAMAS_F32)
+        sweep_solo<true>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
+    else
+        sweep_solo<false>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
+}
+
 }  // namespace
 
 size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident) {
@@ -858,4 +1347,19 @@ cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, damas_sweep_kernel, p);
+}
+
+size_t sweep_solo_smem_bytes(int R, int dtype) {
+    const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
+    return 128 + (size_t)SOLO_SLOTS * 4 * 32 * 32 * elt + (size_t)4 * R * sizeof(float) +
+           (size_t)2 * SOLO_STAGE * R * elt;
+}
+
+cudaError_t launch_sweep_solo(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(damas_sweep_solo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // no CTA waits on another: a plain launch, one CTA per system
+    damas_sweep_solo_kernel<<<p.nsys, SOLO_THREADS, smem, st>>>(p, maps);
+    return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
 // Descriptors of the persistent Gauss-Seidel launch.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,3 +31,12 @@ static_assert(sizeof(SweepParams) <= 32000, "kernel parameter block");
 size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident);
 cudaError_t sweep_occupancy(size_t smem, int *blocks_per_sm);
 cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream_t st);
+// the single-CTA form: one CTA per system (S > 96), A streamed, no hand-overs;
+// bit-identical iterates and state to the team form
+// Tensor maps over each system's At (32 x 32 boxes), built by make_sweep_tile_map.
+struct SoloMaps {
+    CUtensorMap m[SWEEP_MAX_SYS];
+};
+size_t sweep_solo_smem_bytes(int R, int dtype);
+bool make_sweep_tile_map(CUtensorMap *m, const void *At, int dtype, int lda, int S);
+cudaError_t launch_sweep_solo(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st);

@@ -27,9 +27,12 @@ def test_solve_plan(ctx):
             nb = -(-S // 32)
             assert R % 32 == 0 and n * R >= nb * 32 and (n - 1) * R < nb * 32
             assert 1 <= n <= max(1, sms)
-    # the compressed 81x81 system keeps A in shared memory; the full grid streams it
-    assert D.damas_solve_plan(ctx, 657, D.F32)[2]
-    assert not D.damas_solve_plan(ctx, 6561, D.F32)[2]
+    # the compressed 81x81 system runs on one CTA (no hand-overs); asked to keep A in
+    # shared memory, it takes a resident team; the full grid streams A
+    assert D.damas_solve_plan(ctx, 657, D.F32) == (1, 672, False)
+    n, R, res = D.damas_solve_plan(ctx, 657, D.F32, a_placement=D.PLACE_RESIDENT)
+    assert res and n > 1
+    assert not D.damas_solve_plan(ctx, 6561, D.F32)[2] and D.damas_solve_plan(ctx, 6561, D.F32)[0] > 1
     # forced team sizes and placements are honoured
     assert D.damas_solve_plan(ctx, 657, D.F32, ctas=21, a_placement=D.PLACE_STREAM) == (21, 32, False)
     n, R, res = D.damas_solve_plan(ctx, 657, D.F32, a_placement=D.PLACE_STREAM)
