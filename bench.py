@@ -355,12 +355,14 @@ def run_gpu(args, rank, world, local_rank):
         "full_grid": {"value": round(full_bins, 3), "unit": UNIT, "ms_per_bin": round(tot_f / k_full, 3),
                       "steps": k_full, "sweep_ms": round(sweep_f_ms, 3), "sweep_gbs": round(ach_f, 1),
                       "speedup_compressed_vs_full": round(value / full_bins, 2)},
-        "roofline": {"kernel": "damas_sweep_kernel (compressed grid)", "bound": "hbm", "achieved": round(ach_c, 1),
+        "roofline": {"kernel": "damas_sweep_solo_kernel (compressed grid: the single-CTA form)", "bound": "hbm",
+                     "achieved": round(ach_c, 1),
                      "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_c / hbm_peak, 4),
                      "traffic": traffic.get("sweep_spiral81_compressed"), "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_c, "launch_ms": round(sweep_c_ms, 4),
-                     "note": "A (S~ x S~ FP32, 1.7 MB) is read once per sweep in the algorithm; the kernel keeps it "
-                             "in shared memory, so the launch is bound by the sequential row chain, not HBM"},
+                     "note": "A (S~ x S~ FP32, 1.7 MB) is read once per sweep in the algorithm; the kernel reads "
+                             "it from L2 (tiles by TMA, fold entries by asynchronous copies) and from DRAM about "
+                             "once per launch, so the launch is bound by the sequential row chain, not HBM"},
         "roofline_full_grid": {"kernel": "damas_sweep_kernel (full grid)", "bound": "hbm", "achieved": round(ach_f, 1),
                                "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_f / hbm_peak, 4),
                                "traffic": traffic.get("sweep_spiral81_full"), "algorithmic_bytes_per_launch": bytes_f,

@@ -52,7 +52,6 @@
 #include <type_traits>
 
 #include "common.cuh"
-#include "sweep.cuh"
 
 namespace {
 
@@ -537,22 +536,6 @@ bool make_map(CUtensorMap *m, const float *plane, int ldm, int S) {
 }
 
 }  // namespace
-
-// Tensor map over a system's At for the single-CTA Gauss-Seidel form (FP32 or
-// BF16, S rows of lda values): unswizzled 32 x 32 boxes; rows past S read as zeros.
-bool make_sweep_tile_map(CUtensorMap *m, const void *At, int dtype, int lda, int S) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
-    const cuuint64_t dims[2] = {(cuuint64_t)lda, (cuuint64_t)S};
-    const cuuint64_t strides[1] = {(cuuint64_t)lda * elt};
-    const cuuint32_t box[2] = {32, 32};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(m, dtype == DAMAS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-              const_cast<void *>(At), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-           CUDA_SUCCESS;
-}
 
 static size_t psf_smem_bytes() { return SMEM_BYTES + 1024; }
 size_t psf_work_floats(int S, int ldm, bool symmetric) { return (size_t)S * 2 * ldm * (symmetric ? 2 : 4); }

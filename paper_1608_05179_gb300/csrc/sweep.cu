@@ -39,6 +39,8 @@
 // Systems of one block run the same steps without the overlap.  At the end x,
 // the residual and the two dx blocks not yet folded into every row are written
 // out, so a later call continues bit for bit.
+#include <mutex>
+
 #include "common.cuh"
 
 #include "sweep.cuh"
@@ -1353,6 +1355,34 @@ size_t sweep_solo_smem_bytes(int R, int dtype) {
     const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
     return 128 + (size_t)SOLO_SLOTS * 4 * 32 * 32 * elt + (size_t)4 * R * sizeof(float) +
            (size_t)2 * SOLO_STAGE * R * elt;
+}
+
+// Tensor map over a system's At for the single-CTA form (FP32 or BF16, S rows of
+// lda values): unswizzled 32 x 32 boxes; rows past S read as zeros.
+bool make_sweep_tile_map(CUtensorMap *m, const void *At, int dtype, int lda, int S) {
+    using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(f);
+    });
+    if (!fn) return false;
+    const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
+    const cuuint64_t dims[2] = {(cuuint64_t)lda, (cuuint64_t)S};
+    const cuuint64_t strides[1] = {(cuuint64_t)lda * elt};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, dtype == DAMAS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+              const_cast<void *>(At), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
 }
 
 cudaError_t launch_sweep_solo(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st) {
