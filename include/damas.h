@@ -338,23 +338,35 @@ typedef struct {
  * of sweeps.
  *   sys    host array of nsys descriptors (copied before the call returns).
  *   cfg    optional (NULL = defaults).
- * Each system is solved by a team of CTAs that run concurrently (a cooperative
- * launch; every team must fit on the device at once).  Every device-side wait
- * is bounded by cfg->timeout_ms; a wait that runs out makes the kernel stop and
- * report DAMAS_ETIMEDOUT.  Without cfg->status_dev the call synchronises the
- * stream and returns that status; with it the call returns at once and the
- * status lands in *status_dev.
+ * A system runs in one of two forms with bit-identical results (x and state):
+ *  - single CTA: one CTA of 512 threads holds the whole system's x and
+ *    residual, reads A from global memory (tiles by TMA, fold entries by
+ *    asynchronous copies a step ahead) and hands nothing to other CTAs.  Used
+ *    for a system of 97 or more rows whose rows fit the CTA's shared memory
+ *    when it is asked for one CTA (ctas = 1) with a_placement 0 or 2, or, by
+ *    default, when it has at most 1024 rows; and only when every system of the
+ *    call takes this form (such a launch needs no co-residency, so any number
+ *    of systems run in it);
+ *  - team: CTAs that run concurrently (a cooperative launch, or one
+ *    thread-block cluster per team when all teams are equal, 2-16 CTAs, and fit
+ *    at once; every team must fit on the device at once) own contiguous row
+ *    blocks and hand each block's dx on through global memory.
+ * Every device-side wait is bounded by cfg->timeout_ms; a wait that runs out
+ * makes the kernel stop and report DAMAS_ETIMEDOUT.  Without cfg->status_dev
+ * the call synchronises the stream and returns that status; with it the call
+ * returns at once and the status lands in *status_dev.
  */
 int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg,
                 damas_stream stream);
 
 /*
- * The plan damas_solve would choose for one system of S rows (host only; no
- * device work): CTAs in its team, rows per CTA, and whether the CTAs keep their
- * rows of A in shared memory (1) or stream them (0).  ctas and a_placement mean
- * what damas_solve_cfg's ctas_per_system and a_placement mean.  Blocks of 32
- * rows are owned contiguously, so one sweep hands the iteration from CTA to CTA
- * *ncta_out times when *ncta_out > 1.
+ * The plan damas_solve would choose for one system of S rows when it is the
+ * only system of the call (host only; no device work): CTAs in its team, rows
+ * per CTA, and whether the CTAs keep their rows of A in shared memory (1) or
+ * stream them (0).  ctas and a_placement mean what damas_solve_cfg's
+ * ctas_per_system and a_placement mean.  *ncta_out = 1 with S >= 97 is the
+ * single-CTA form.  Blocks of 32 rows are owned contiguously, so one sweep hands
+ * the iteration from CTA to CTA *ncta_out times when *ncta_out > 1.
  */
 int damas_solve_plan(damas_ctx *ctx, int S, int lda, int a_dtype, int ctas, int a_placement, int *ncta_out,
                      int *rows_per_cta_out, int *resident_out);
