@@ -1,5 +1,7 @@
 // DAMAS Gauss-Seidel iteration with the non-negativity clamp (§3, Eq. (13)-(14)),
-// as one persistent cooperative launch over a batch of independent systems.
+// one persistent launch over a batch of independent systems, in two forms with
+// bit-identical results: teams of CTAs (below) and one CTA per system (the
+// single-CTA form, further down).
 //
 // Rows are cut into blocks of 32 in the paper's order (block J = rows
 // 32J..32J+31) and processed as the sequence of steps G = t*nb + J (sweep t,
