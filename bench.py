@@ -388,13 +388,17 @@ def _handover_floor(D, ctx, S_sub, S, sweep_c_ms, sweep_f_ms):
            "what": "iters x (CTA-to-CTA hand-overs per sweep) x median one-way hand-over, against the launch"}
     for name, n, ms in (("compressed", S_sub, sweep_c_ms), ("full_grid", S, sweep_f_ms)):
         ncta, rows, res = D.damas_solve_plan(ctx, n, D.F32)
-        floor = ITERS * (ncta if ncta > 1 else 0) * med / 1e6
         out[name] = {"team_ctas": ncta, "rows_per_cta": rows, "blocks_per_sweep": -(-n // 32),
-                     "handovers_per_sweep": ncta if ncta > 1 else 0, "floor_ms": round(floor, 3),
-                     "launch_ms": round(ms, 3), "frac": round(floor / ms, 3),
+                     "handovers_per_sweep": ncta if ncta > 1 else 0, "launch_ms": round(ms, 3),
                      "step_ns": round(ms * 1e6 / (ITERS * -(-n // 32)), 1)}
-        if ncta == 1:
-            out[name]["form"] = "single CTA: no hand-overs; each 32-row step is the row chain and one CTA barrier"
+        if ncta > 1:
+            floor = ITERS * ncta * med / 1e6
+            out[name].update({"floor_ms": round(floor, 3), "frac": round(floor / ms, 3)})
+        else:
+            # no hand-overs: the floor above does not apply (null rather than 0)
+            out[name].update({"floor_ms": None, "frac": None,
+                              "form": "single CTA: no hand-overs; each 32-row step is the row chain and one "
+                                      "CTA barrier"})
 
     return out
 
