@@ -3,8 +3,9 @@
 Hand-derived iterates on 2x2 and 3x3 systems (they separate Gauss-Seidel from
 Jacobi and catch index slips), the unconstrained limit (a library linear solve),
 the fixed-point (KKT) conditions, monotone descent of the quadratic for symmetric
-PSD A, exhaustive brute force over supports on tiny grids, and the recovery of
-an on-grid monopole (§5 Case 1).
+PSD A, exhaustive brute force over supports on tiny grids, the unique NNLS
+optimum (a library active-set solver) on 5x5 grids, and the recovery of an
+on-grid monopole (§5 Case 1).
 """
 import itertools
 
@@ -157,3 +158,28 @@ def test_compressed_pipeline_end_to_end():
     assert 0.095 * 6561 <= len(out["idx"]) <= 0.12 * 6561
     assert abs(out["x"].sum() - sc.powers.sum()) < 0.15 * sc.powers.sum()
     assert out["x"].min() >= 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_nnls_optimum_on_5x5_grids(seed):
+    """5x5 grids (25 unknowns, too many supports to enumerate): with 8
+    microphones the PSF matrix is positive definite, so min 0.5 x^T A x - b^T x
+    over x >= 0 is the non-negative least-squares problem min |L x - y| with
+    A = L^T L and L^T y = b, whose minimiser is unique.  The Lawson-Hanson NNLS
+    of scipy gives it; the Gauss-Seidel iteration with the clamp must reach the
+    same x after many sweeps."""
+    so = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(seed)
+    mics = synth.mic_disc(8, 0.5, rng)
+    grid = synth.square_plane(5, 0.6, 1.0)
+    pts = grid.points()
+    src = np.array([[0.05, -0.1, 1.0], [-0.2, 0.15, 1.0]])
+    C = synth.simulate_csm(mics, src, np.array([1.0, 0.6]), 2500.0, 343.0, 25.0, rng)
+    A, _ = O.psf_matrix(mics, pts, 2500.0, 343.0, O.FORM_E)
+    b = O.das_map(mics, pts, 2500.0, 343.0, C, O.FORM_E)
+    assert np.linalg.eigvalsh(A).min() > 1e-3
+    L = np.linalg.cholesky(A).T
+    x_nnls, _ = so.nnls(L, np.linalg.solve(L.T, b), maxiter=10000)
+    x = O.gauss_seidel(A, b, 20000)
+    assert np.allclose(x, x_nnls, rtol=1e-9, atol=1e-12)
+    assert abs(O.objective(A, b, x) - O.objective(A, b, x_nnls)) <= 1e-12 * abs(O.objective(A, b, x_nnls))
