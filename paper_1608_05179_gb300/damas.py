@@ -274,7 +274,9 @@ PLACE_AUTO, PLACE_RESIDENT, PLACE_STREAM = 0, 1, 2
 def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int = 0,
                 status: torch.Tensor | None = None, a_placement: int = PLACE_AUTO, withhold_block: int = 0,
                 stream=None):
-    """DAMAS Gauss-Seidel sweeps (Eq. (13)-(14)) on a batch of systems in one persistent launch."""
+    """DAMAS Gauss-Seidel sweeps (Eq. (13)-(14)) on a batch of systems in one persistent launch:
+    one CTA per system (small systems, when every system of the call qualifies) or a team
+    of CTAs per system; both forms give bit-identical x and state."""
     if isinstance(systems, System):
         systems = [systems]
     arr = (_lib.damas_system * len(systems))(*[s.cstruct() for s in systems])
@@ -287,7 +289,8 @@ def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int
 
 def damas_solve_plan(ctx: Context, S: int, a_dtype: int = F32, ctas: int = 0, a_placement: int = PLACE_AUTO,
                      lda: int | None = None):
-    """The team damas_solve would use for one system: (CTAs, rows per CTA, resident)."""
+    """The plan damas_solve would use for one system alone: (CTAs, rows per CTA, resident).
+    One CTA for S >= 97 is the single-CTA form (no hand-overs between CTAs)."""
     n, r, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     ctx.check(ctx.lib.damas_solve_plan(ctx.handle, int(S), int(damas_lda(S) if lda is None else lda), int(a_dtype),
                                        int(ctas), int(a_placement), ctypes.byref(n), ctypes.byref(r),
