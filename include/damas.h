@@ -100,6 +100,32 @@ int damas_create(damas_ctx **out, int device);
 int damas_destroy(damas_ctx *ctx);
 /* Message of the last failed call on ctx (static storage owned by ctx). */
 const char *damas_last_error(const damas_ctx *ctx);
+/* Context options (damas_set_option). */
+enum {
+    /* Bound, in milliseconds (1..600000, default 2000), on every device-side wait
+     * of the build kernels (the PSF Gram of damas_build_psf / damas_build_psf_dr). */
+    DAMAS_OPT_BUILD_TIMEOUT_MS = 1,
+    /* Test hook of those bounded waits, 0 in normal use: 1 makes every later PSF
+     * Gram launch on the context first wait for a device flag that nothing sets,
+     * so the wait runs out after the build timeout and the launch takes its abort
+     * path (no GPU fault is involved).  Set it back to 0 to build normally. */
+    DAMAS_OPT_TEST_HOLD_BUILD = 2
+};
+int damas_set_option(damas_ctx *ctx, int option, long long value);
+
+/*
+ * Synchronise `stream` and report whether a build kernel enqueued on this
+ * context gave up a bounded device wait since the last damas_check:
+ * DAMAS_ETIMEDOUT (the status is then cleared) or DAMAS_OK.  The build calls
+ * (damas_build_psf, damas_build_psf_dr) return as soon as their kernels are
+ * enqueued, so a wait that runs out inside them cannot be their return value:
+ * the Gram writes NaN where it stopped, lets its in-flight loads land, and sets
+ * the context's build status, which damas_check reads and every later
+ * damas_solve on the context sees (it then reports DAMAS_ETIMEDOUT and leaves
+ * x and the state untouched) until damas_check clears it.
+ */
+int damas_check(damas_ctx *ctx, damas_stream stream);
+
 /* Row stride, in elements, that the library uses for an S x S matrix A:
  * S rounded up to a multiple of 32 (every row 128-byte aligned for FP32). */
 int damas_lda(int S);
@@ -124,7 +150,9 @@ int damas_state_floats(int S);
  *             (formulation E uses it to turn x' into power).
  * Steering and propagation vectors are formed with the phase k*d in FP64,
  * reduced to a fraction of a period before an FP32 sine/cosine; the complex
- * Gram products accumulate in FP32.
+ * Gram products accumulate in FP32.  The Gram's device waits are bounded
+ * (DAMAS_OPT_BUILD_TIMEOUT_MS); one that runs out is reported by damas_check
+ * and by the next damas_solve on the context, not by this call.
  */
 int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev,
                     int S_sub, int a_dtype, void *A_dev, int lda, float *gnorm2_dev, damas_stream stream);
@@ -228,7 +256,11 @@ int wavelet_compress_grid(damas_ctx *ctx, const float *b_dev, int nx, int ny, co
  *    points are rejected with DAMAS_EINVAL and nothing is enqueued.
  *  - The first call on a device looks up the array's device address (once per
  *    device, under a lock, with that device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: after a cudaDeviceReset (which also invalidates every context and
+ *    its scratch) this entry point must not be used on that device again.
+ *  - Limits are those of wavelet_compress_grid (nx, ny in 1..65535) and, in
+ *    addition, nx*ny <= DAMAS_NOALLOC_MAX_POINTS.
  *  - Every call on a device uses the same array, which keeps whatever the last
  *    call left there (nothing in it has to start at zero: each call writes every
  *    entry it reads).  Calls whose work overlaps on the GPU (different streams,
@@ -400,10 +432,23 @@ int damas_handover_probe(damas_ctx *ctx, int rounds, int max_pairs, int timeout_
  * 0, PSF matrix, Gauss-Seidel from x = 0, power map.  The result of a request
  * does not depend on what else is in flight (bit for bit).
  */
+/* Admission: a queued request starts (stage 1: uploads, DAS maps, compressed
+ * grids) when a pool slot is free and its stage-1 memory plus the least its
+ * stage 2 can need (every bin keeps at least G^0, and ceil(f S) points with a
+ * keep fraction f) fit hbm_budget_bytes beside the requests in flight; its
+ * matrices and solve (stage 2) are admitted when their memory fits the budget
+ * and the solve's share of the SMs fits the free sm_slots.  A request that does
+ * not fit even alone runs when nothing else is in flight, and stage 2 is always
+ * granted when no other request is solving, so a small budget slows the loop
+ * but never stalls it (the budget can then be exceeded by that one request). */
 typedef struct {
     size_t hbm_budget_bytes; /* device memory the loop may hold for requests; 0 = half the free memory */
     int max_inflight;        /* requests on the device at once; 0 = 32 */
-    int sm_slots;            /* CTAs that concurrent solves may hold together; 0 = twice the SM count */
+    int sm_slots;            /* half-SM units that concurrent solves may hold together; 0 = twice the SM
+                                count (the whole device).  A solve is charged by the library's plan of
+                                it: a CTA that fills its SM (one CTA per SM: the single-CTA form,
+                                teams holding A in shared memory) counts 2, a CTA of a launch that
+                                fits two or more per SM counts 1 */
     int rows_per_cta;        /* solver team size target, rows per CTA; 0 = 768 */
 } damas_serve_cfg;
 
@@ -426,7 +471,11 @@ typedef struct {
     const float *x;            /* host, n_bins x S power maps (valid until the ticket is released) */
     const double *total_power; /* host, n_bins integrated powers */
     const int *S_sub;          /* host, n_bins compressed sizes */
-    double t_submit, t_admit, t_done; /* seconds on the host steady clock */
+    double t_submit, t_admit, t_done; /* seconds on the host steady clock: submitted, admitted
+                                         (stage 1: uploads, DAS maps, compressed grids), done */
+    double t_solve;            /* when its matrices and solve were admitted (stage 2) */
+    size_t hbm_bytes;          /* device memory charged to the request against hbm_budget_bytes */
+    int sm_units;              /* half-SM units its solve was charged (see damas_serve_cfg.sm_slots) */
 } damas_result;
 
 /* Start the loop's worker thread on ctx's device. */

@@ -14,6 +14,7 @@ F32, BF16 = 1, 2
 PRED_LINEAR, PRED_HAAR = 0, 1
 EPS_ABS, EPS_REL_MAX, EPS_KEEP_FRAC = 0, 1, 2
 INIT_ZERO, INIT_X, INIT_STATE = 0, 1, 2
+OPT_BUILD_TIMEOUT_MS, OPT_TEST_HOLD_BUILD = 1, 2
 
 ERROR_NAMES = {0: "DAMAS_OK", -1: "DAMAS_EINVAL", -2: "DAMAS_ENOMEM", -3: "DAMAS_ECUDA", -4: "DAMAS_ETIMEDOUT",
                -5: "DAMAS_EBUSY", -6: "DAMAS_ENOTFOUND"}
@@ -55,7 +56,8 @@ class damas_request(ctypes.Structure):
 class damas_result(ctypes.Structure):
     _fields_ = [("status", c_int), ("n_bins", c_int), ("S", c_int), ("x", ctypes.POINTER(ctypes.c_float)),
                 ("total_power", ctypes.POINTER(c_double)), ("S_sub", ctypes.POINTER(c_int)),
-                ("t_submit", c_double), ("t_admit", c_double), ("t_done", c_double)]
+                ("t_submit", c_double), ("t_admit", c_double), ("t_done", c_double), ("t_solve", c_double),
+                ("hbm_bytes", ctypes.c_size_t), ("sm_units", c_int)]
 
 
 # every symbol include/damas.h declares, with its signature
@@ -63,6 +65,8 @@ SIGNATURES = {
     "damas_create": (c_int, [ctypes.POINTER(c_void_p), c_int]),
     "damas_destroy": (c_int, [c_void_p]),
     "damas_last_error": (ctypes.c_char_p, [c_void_p]),
+    "damas_set_option": (c_int, [c_void_p, c_int, ctypes.c_longlong]),
+    "damas_check": (c_int, [c_void_p, c_void_p]),
     "damas_lda": (c_int, [c_int]),
     "damas_state_floats": (c_int, [c_int]),
     "damas_build_psf": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_int, c_void_p,

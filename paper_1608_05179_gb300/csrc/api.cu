@@ -89,6 +89,18 @@ GeomK to_kernel(const damas_geom *g, double f) {
 
 inline int planes_ld(int M) { return round_up(M, 16); }  // whole 16-microphone chunks for the Gram
 
+// The context's build status word (device int, zero until a build kernel's
+// bounded wait runs out); allocated and cleared on first use.
+int ctx_kstat(damas_ctx *ctx, int **out) {
+    if (!ctx->kstat.ptr) {
+        int rc = ctx_ensure(ctx, ctx->kstat, 256);
+        if (rc) return rc;
+        DAMAS_CUDA_TRY(ctx, cudaMemset(ctx->kstat.ptr, 0, ctx->kstat.cap));
+    }
+    *out = (int *)ctx->kstat.ptr;
+    return DAMAS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -119,7 +131,8 @@ int damas_destroy(damas_ctx *ctx) {
     {
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();
-        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc, &ctx->pad, &ctx->probe})
+        for (ScratchBuf *b : {&ctx->planes, &ctx->wave, &ctx->solve, &ctx->status, &ctx->misc, &ctx->pad, &ctx->probe,
+                              &ctx->kstat})
             if (b->ptr) cudaFree(b->ptr);
     }
     delete ctx;
@@ -127,6 +140,36 @@ int damas_destroy(damas_ctx *ctx) {
 }
 
 const char *damas_last_error(const damas_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int damas_set_option(damas_ctx *ctx, int option, long long value) {
+    if (!ctx) return DAMAS_EINVAL;
+    switch (option) {
+        case DAMAS_OPT_BUILD_TIMEOUT_MS:
+            if (value < 1 || value > 600000) return ctx_fail(ctx, DAMAS_EINVAL, "build timeout %lld ms", value);
+            ctx->build_timeout_ms = (int)value;
+            return DAMAS_OK;
+        case DAMAS_OPT_TEST_HOLD_BUILD:
+            if (value != 0 && value != 1) return ctx_fail(ctx, DAMAS_EINVAL, "test hold must be 0 or 1");
+            ctx->test_hold = (int)value;
+            return DAMAS_OK;
+        default:
+            return ctx_fail(ctx, DAMAS_EINVAL, "unknown option %d", option);
+    }
+}
+
+int damas_check(damas_ctx *ctx, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    DAMAS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (!ctx->kstat.ptr) return DAMAS_OK;
+    int h = 0;
+    DAMAS_CUDA_TRY(ctx, cudaMemcpy(&h, ctx->kstat.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h == 0) return DAMAS_OK;
+    DAMAS_CUDA_TRY(ctx, cudaMemset(ctx->kstat.ptr, 0, sizeof(int)));
+    return ctx_fail(ctx, h, "a build kernel's device wait ran out (limit %d ms); its output holds NaN",
+                    ctx->build_timeout_ms);
+}
 
 int damas_lda(int S) { return S <= 0 ? 0 : round_up(S, 32); }
 
@@ -162,8 +205,12 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     const int kind = geom->formulation == DAMAS_FORM_P ? 2 : 0;
     DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, idx_dev, S_sub, Lre, Lim, Rre, Rim, ldm, gnorm2_dev, st));
     const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
+    int *kst = nullptr;
+    rc = ctx_kstat(ctx, &kst);
+    if (rc) return rc;
     DAMAS_CUDA_TRY(ctx, launch_psf_gram(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, a_dtype,
-                                        base + plane * nplanes, st));
+                                        base + plane * nplanes, kst, (unsigned long long)ctx->build_timeout_ms * 1000000ull,
+                                        ctx->test_hold, st));
     return DAMAS_OK;
 }
 
@@ -194,8 +241,12 @@ int damas_build_psf_dr(damas_ctx *ctx, const damas_geom *geom, double freq_hz, c
     const int kind = geom->formulation == DAMAS_FORM_P ? 2 : 0;
     DAMAS_CUDA_TRY(ctx, launch_steer(gk, kind, idx_dev, S_sub, Lre, Lim, Rre, Rim, ldm, gnorm2_dev, st));
     const float scale = geom->formulation == DAMAS_FORM_P ? (float)(1.0 / ((double)geom->M * geom->M)) : 1.0f;
+    int *kst = nullptr;
+    rc = ctx_kstat(ctx, &kst);
+    if (rc) return rc;
     DAMAS_CUDA_TRY(ctx, launch_psf_gram(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, DAMAS_F32,
-                                        base + plane * nplanes, st));
+                                        base + plane * nplanes, kst, (unsigned long long)ctx->build_timeout_ms * 1000000ull,
+                                        ctx->test_hold, st));
     DAMAS_CUDA_TRY(ctx, launch_psf_dr(Lre, Lim, Rre, Rim, ldm, geom->M, S_sub, scale, A_dev, lda, dscale_dev, st));
     return DAMAS_OK;
 }
@@ -386,7 +437,127 @@ Plan plan_system(const damas_ctx *ctx, const damas_system &s, int forced, int pl
     return p;
 }
 
+struct Launch {
+    std::vector<int> ids;
+    size_t smem = 0;
+    int ctas = 0;
+    int max_iters = 0;
+    int solo = 0;
+};
+
+// Plan every system of a damas_solve call, then pack them into launches that
+// fit on the device at once (systems already validated).
+int plan_solve(damas_ctx *ctx, const damas_system *sys, int nsys, int forced, int placement,
+               std::vector<Plan> &plans, std::vector<Launch> &launches) {
+    // plan every system, then pack them into launches that fit on the device at once
+    plans.assign(nsys, Plan());
+    for (int i = 0; i < nsys; ++i)
+        plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement, ctx->sm_count);
+    {
+        // The single-CTA form runs in a launch of its own.  A call that also holds
+        // teams keeps every system in the teams' one launch (launches on a stream
+        // run one after another), so there the single-CTA systems become one-CTA
+        // teams.
+        int nsolo = 0;
+        for (const Plan &q : plans) nsolo += q.solo;
+        if (nsolo > 0 && nsolo < nsys)
+            for (int i = 0; i < nsys; ++i)
+                if (plans[i].solo)
+                    plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement,
+                                           ctx->sm_count, false);
+    }
+    if (placement == 0 && nsys > 1) {
+        // A batch whose resident teams need more than one launch (a resident CTA
+        // fills an SM) but whose streamed teams fit in one (two CTAs per SM) is
+        // streamed: the teams then run side by side.  Results do not depend on the
+        // placement.
+        auto fits_once = [&](const std::vector<Plan> &pl) -> bool {
+            size_t smem = 0;
+            int ctas = 0;
+            for (const Plan &q : pl) {
+                smem = std::max(smem, q.smem);
+                ctas += q.ncta;
+            }
+            int occ = 0;
+            if (nsys > SWEEP_MAX_SYS || sweep_occupancy(smem, &occ) != cudaSuccess) return false;
+            return ctas <= occ * ctx->sm_count;
+        };
+        bool any_res = false;
+        for (const Plan &q : plans) any_res |= q.resident != 0;
+        if (any_res && !fits_once(plans)) {
+            std::vector<Plan> streamed(nsys);
+            for (int i = 0; i < nsys; ++i)
+                streamed[i] = plans[i].resident
+                                  ? plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, 2, ctx->sm_count,
+                                                false)
+                                  : plans[i];
+            if (fits_once(streamed)) plans.swap(streamed);
+        }
+        cudaGetLastError();
+    }
+    for (int i = 0; i < nsys; ++i) {
+        if (plans[i].smem > ctx->smem_optin - 1024)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: %zu bytes of shared memory per CTA do not fit", i,
+                            plans[i].smem);
+        if (plans[i].solo) continue;
+        int occ = 0;
+        cudaError_t e = sweep_occupancy(plans[i].smem, &occ);
+        if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+        if (plans[i].ncta > occ * ctx->sm_count)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d needs %d co-resident CTAs, the device holds %d", i,
+                            plans[i].ncta, occ * ctx->sm_count);
+    }
+    launches.clear();
+    {
+        // a launch holds either single-CTA systems (any number of CTAs: none waits
+        // on another) or teams (all co-resident)
+        Launch cur;
+        for (int i = 0; i < nsys; ++i) {
+            const Plan &pl = plans[i];
+            bool flush = !cur.ids.empty() && ((int)cur.ids.size() == SWEEP_MAX_SYS || cur.solo != pl.solo);
+            if (!flush && !pl.solo && !cur.ids.empty()) {
+                int occ = 0;
+                cudaError_t e = sweep_occupancy(std::max(cur.smem, pl.smem), &occ);
+                if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+                flush = cur.ctas + pl.ncta > occ * ctx->sm_count;
+            }
+            if (flush) {
+                launches.push_back(cur);
+                cur = Launch();
+            }
+            cur.solo = pl.solo;
+            cur.ids.push_back(i);
+            cur.smem = std::max(cur.smem, pl.smem);
+            cur.ctas += pl.ncta;
+            cur.max_iters = std::max(cur.max_iters, sys[i].iters);
+        }
+        if (!cur.ids.empty()) launches.push_back(cur);
+    }
+    return DAMAS_OK;
+}
+
 }  // namespace
+
+}  // extern "C"
+
+int solve_half_sm_units(damas_ctx *ctx, const damas_system *sys, int nsys, int *units) {
+    std::vector<Plan> plans;
+    std::vector<Launch> launches;
+    int rc = plan_solve(ctx, sys, nsys, 0, 0, plans, launches);
+    if (rc) return rc;
+    int most = 0;
+    for (const Launch &L : launches) {
+        int occ = 0;
+        cudaError_t e = L.solo ? sweep_solo_occupancy(L.smem, &occ) : sweep_occupancy(L.smem, &occ);
+        if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+        const int per_cta = occ >= 2 ? 1 : 2;  // a CTA that fills its SM holds both halves
+        most = std::max(most, L.ctas * per_cta);
+    }
+    *units = most;
+    return DAMAS_OK;
+}
+
+extern "C" {
 
 int damas_solve_plan(damas_ctx *ctx, int S, int lda, int a_dtype, int ctas, int a_placement, int *ncta_out,
                      int *rows_per_cta_out, int *resident_out) {
@@ -455,97 +626,10 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
 
-    // plan every system, then pack them into launches that fit on the device at once
-    std::vector<Plan> plans(nsys);
-    for (int i = 0; i < nsys; ++i)
-        plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement, ctx->sm_count);
-    {
-        // The single-CTA form runs in a launch of its own.  A call that also holds
-        // teams keeps every system in the teams' one launch (launches on a stream
-        // run one after another), so there the single-CTA systems become one-CTA
-        // teams.
-        int nsolo = 0;
-        for (const Plan &q : plans) nsolo += q.solo;
-        if (nsolo > 0 && nsolo < nsys)
-            for (int i = 0; i < nsys; ++i)
-                if (plans[i].solo)
-                    plans[i] = plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, placement,
-                                           ctx->sm_count, false);
-    }
-    if (placement == 0 && nsys > 1) {
-        // A batch whose resident teams need more than one launch (a resident CTA
-        // fills an SM) but whose streamed teams fit in one (two CTAs per SM) is
-        // streamed: the teams then run side by side.  Results do not depend on the
-        // placement.
-        auto fits_once = [&](const std::vector<Plan> &pl) -> bool {
-            size_t smem = 0;
-            int ctas = 0;
-            for (const Plan &q : pl) {
-                smem = std::max(smem, q.smem);
-                ctas += q.ncta;
-            }
-            int occ = 0;
-            if (nsys > SWEEP_MAX_SYS || sweep_occupancy(smem, &occ) != cudaSuccess) return false;
-            return ctas <= occ * ctx->sm_count;
-        };
-        bool any_res = false;
-        for (const Plan &q : plans) any_res |= q.resident != 0;
-        if (any_res && !fits_once(plans)) {
-            std::vector<Plan> streamed(nsys);
-            for (int i = 0; i < nsys; ++i)
-                streamed[i] = plans[i].resident
-                                  ? plan_system(ctx, sys[i], sys[i].ctas > 0 ? sys[i].ctas : forced, 2, ctx->sm_count,
-                                                false)
-                                  : plans[i];
-            if (fits_once(streamed)) plans.swap(streamed);
-        }
-        cudaGetLastError();
-    }
-    for (int i = 0; i < nsys; ++i) {
-        if (plans[i].smem > ctx->smem_optin - 1024)
-            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: %zu bytes of shared memory per CTA do not fit", i,
-                            plans[i].smem);
-        if (plans[i].solo) continue;
-        int occ = 0;
-        cudaError_t e = sweep_occupancy(plans[i].smem, &occ);
-        if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-        if (plans[i].ncta > occ * ctx->sm_count)
-            return ctx_fail(ctx, DAMAS_EINVAL, "system %d needs %d co-resident CTAs, the device holds %d", i,
-                            plans[i].ncta, occ * ctx->sm_count);
-    }
-    struct Launch {
-        std::vector<int> ids;
-        size_t smem = 0;
-        int ctas = 0;
-        int max_iters = 0;
-        int solo = 0;
-    };
+    std::vector<Plan> plans;
     std::vector<Launch> launches;
-    {
-        // a launch holds either single-CTA systems (any number of CTAs: none waits
-        // on another) or teams (all co-resident)
-        Launch cur;
-        for (int i = 0; i < nsys; ++i) {
-            const Plan &pl = plans[i];
-            bool flush = !cur.ids.empty() && ((int)cur.ids.size() == SWEEP_MAX_SYS || cur.solo != pl.solo);
-            if (!flush && !pl.solo && !cur.ids.empty()) {
-                int occ = 0;
-                cudaError_t e = sweep_occupancy(std::max(cur.smem, pl.smem), &occ);
-                if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-                flush = cur.ctas + pl.ncta > occ * ctx->sm_count;
-            }
-            if (flush) {
-                launches.push_back(cur);
-                cur = Launch();
-            }
-            cur.solo = pl.solo;
-            cur.ids.push_back(i);
-            cur.smem = std::max(cur.smem, pl.smem);
-            cur.ctas += pl.ncta;
-            cur.max_iters = std::max(cur.max_iters, sys[i].iters);
-        }
-        if (!cur.ids.empty()) launches.push_back(cur);
-    }
+    int prc = plan_solve(ctx, sys, nsys, forced, placement, plans, launches);
+    if (prc) return prc;
     // exchange buffers: per system nb*32 mailbox words (epoch << 32 | bits(dx)),
     // sized for the largest launch.  The region only ever holds mailbox words,
     // and epochs grow from launch to launch, so stale words always read as old.
@@ -589,6 +673,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         p.status = status;
         p.timeout_ns = (unsigned long long)timeout_ms * 1000000ull;
         p.withhold_block = (cfg && cfg->withhold_block > 0) ? cfg->withhold_block - 1 : -1;
+        p.upstream = (const int *)ctx->kstat.ptr;
         unsigned long long *mb = (unsigned long long *)ctx->solve.ptr;
         int cta = 0;
         for (int q = 0; q < p.nsys; ++q) {
@@ -631,7 +716,11 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     int h = 0;
     DAMAS_CUDA_TRY(ctx, cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     DAMAS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    if (h != 0) return ctx_fail(ctx, h, "solver wait timed out after %lld ms", timeout_ms);
+    if (h != 0)
+        return ctx_fail(ctx, h,
+                        "a device wait ran out: in the solve (limit %lld ms), or in a build kernel of this context "
+                        "before it (damas_check reports and clears that)",
+                        timeout_ms);
     return DAMAS_OK;
 }
 

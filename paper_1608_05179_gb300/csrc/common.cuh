@@ -28,12 +28,21 @@ struct damas_ctx {
     ScratchBuf misc;
     ScratchBuf pad;      // neighbour-padding marks
     ScratchBuf probe;    // hand-over probe words
+    ScratchBuf kstat;    // build status word: DAMAS_ETIMEDOUT once a build kernel's wait ran out (sticky)
+    int build_timeout_ms = 2000;  // bound on the build kernels' device waits
+    int test_hold = 0;            // test hook of those waits (damas_set_option)
     unsigned int epoch = 0;      // mailbox epoch of the solver exchange buffers
     struct ServeState *serve = nullptr;  // serving loop, when started
 };
 void serve_shutdown(damas_ctx *ctx);
 
 int ctx_fail(damas_ctx *ctx, int code, const char *fmt, ...);
+// Half-SM units that a damas_solve call on these systems (default placement and
+// team sizes, as given per system) occupies while its largest launch runs: a CTA
+// that fills its SM (one CTA per SM) counts 2, one of a launch with two or more
+// CTAs per SM counts 1.  The device has 2 * sm_count units.  The calling thread
+// must have the context's device current.
+int solve_half_sm_units(damas_ctx *ctx, const damas_system *sys, int nsys, int *units);
 int ctx_ensure(damas_ctx *ctx, ScratchBuf &b, size_t bytes);
 
 #define DAMAS_CUDA_TRY(ctx, call)                                                              \
@@ -63,9 +72,13 @@ cudaError_t launch_steer(const GeomK &g, int kind, const int32_t *idx, int n, fl
                          float *Rim, int ldm, float *gnorm2, cudaStream_t st);
 // A[n][s] = scale * |sum_m conj(L_nm) R_sm|^2 with unit diagonal, zero padding to
 // lda, on the tensor cores (tcgen05, 3xTF32); ldm must be a multiple of 16 and
-// work must hold psf_work_floats() floats of device scratch.
+// work must hold psf_work_floats() floats of device scratch.  Every device wait
+// is bounded by timeout_ns; one that runs out writes DAMAS_ETIMEDOUT into
+// *status (when status is given, only over 0).  hold = 1 is the test hook of
+// those waits: the operand loader first waits for a flag that nothing sets.
 cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm,
-                            int M, int S, float scale, void *A, int lda, int a_dtype, float *work, cudaStream_t st);
+                            int M, int S, float scale, void *A, int lda, int a_dtype, float *work, int *status,
+                            unsigned long long timeout_ns, int hold, cudaStream_t st);
 size_t psf_work_floats(int S, int ldm, bool symmetric);
 // b_n = scale * Re(L_n^H C L_n) for n < S (dr: without the terms of C's diagonal).
 cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,

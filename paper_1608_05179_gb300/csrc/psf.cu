@@ -38,9 +38,10 @@
 // R the same vectors, formulation E) only tiles that reach the upper triangle
 // run, every value with s >= n is also written mirrored, and A is exactly
 // symmetric.  Every wait is bounded by the global timer; a wait that runs out
-// sets a CTA-wide abort flag, every role stops waiting and the remaining
-// tiles are written as NaN, so a failure shows in the result instead of
-// hanging the device.
+// sets a CTA-wide abort flag, every role stops waiting, the remaining tiles
+// are written as NaN, the operand loads already issued are let land, and the
+// launch reports DAMAS_ETIMEDOUT in its status word, so a failure shows
+// instead of hanging the device.
 //
 // Accuracy: FP32 accumulation in the tensor core truncates, so the result
 // carries a small bias toward zero that grows with the number of MMAs per
@@ -76,7 +77,10 @@ constexpr int TMA_BOX_ROWS = 128;
 static_assert(BM == TMA_BOX_ROWS && BN == TMA_BOX_ROWS, "one TMA box per operand tile");
 static_assert(SMEM_BYTES + 1024 <= 232448, "shared memory of one CTA");
 
-__device__ unsigned int psf_timeouts;
+// Test hook of the bounded waits: a launch with hold = 1 makes its operand
+// loader first wait for this flag, which nothing ever sets, so that wait runs
+// out and the launch takes its abort path (no GPU fault involved).
+__device__ int psf_hold_flag;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -248,7 +252,8 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 template <typename OutT>
 __global__ void __launch_bounds__(THREADS, 1)
     psf_gram_tc_kernel(const __grid_constant__ GramMaps maps, int M, int S, float scale, OutT *__restrict__ A,
-                       int lda, int symmetric, int ntx, int ntiles, unsigned long long timeout_ns) {
+                       int lda, int symmetric, int ntx, int ntiles, unsigned long long timeout_ns, int *status,
+                       int hold) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full_bar[NSTAGE], empty_bar[NSTAGE], acc_full[NACC], acc_empty[NACC],
         done_bar;
@@ -293,9 +298,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == TMA_WARP) {
         if (lane == 0) {
-            // ring position: stage st in its use u (the u-th time it is filled)
+            if (hold) {
+                // the test hook: a bounded wait for a flag that nothing sets
+                const unsigned long long deadline = now_ns() + timeout_ns;
+                while (*(volatile int *)&psf_hold_flag == 0 && !abort_flag)
+                    if (now_ns() > deadline) abort_flag = 1;
+            }
+            // ring position: stage st in its use u (the u-th time it is filled);
+            // last_fill[st]: the use of stage st whose loads were issued last
             int st = 0;
             uint32_t u = 0;
+            int last_fill[NSTAGE];
+            for (int i = 0; i < NSTAGE; ++i) last_fill[i] = -1;
             for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
                 int ty, tx;
                 tile_coords(t, ntx, symmetric, ty, tx);
@@ -314,12 +328,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tma_load_2d(stage + A_TILE, &maps.a_lo, x, n0, bar);
                     tma_load_2d(stage + 2 * A_TILE, &maps.b_hi, x, s0, bar);
                     tma_load_2d(stage + 2 * A_TILE + B_TILE, &maps.b_lo, x, s0, bar);
+                    last_fill[st] = (int)u;
                     if (++st == NSTAGE) {
                         st = 0;
                         ++u;
                     }
                 }
                 if (!ok) break;
+            }
+            if (abort_flag) {
+                // another role gave up: let the loads already issued land before
+                // the CTA exits (bounded; a completed fill's phase reads as done)
+                for (int i = 0; i < NSTAGE; ++i)
+                    if (last_fill[i] >= 0)
+                        mbar_wait(smem_u32(&full_bar[i]), (uint32_t)last_fill[i] & 1u, now_ns() + timeout_ns);
             }
         }
         __syncwarp();
@@ -478,10 +500,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (std::is_same<OutT, float>::value && lane == 0) bulk_wait_all();  // staging tile read and written out
         __syncwarp();
-        if (threadIdx.x == 0 && abort_flag) atomicAdd(&psf_timeouts, 1u);
     }
     fence_before();
     __syncthreads();
+    // a wait that ran out anywhere in the CTA: report it (the launch's output is NaN there)
+    if (threadIdx.x == 0 && abort_flag && status) atomicCAS(status, 0, (int)DAMAS_ETIMEDOUT);
     if (warp == MMA_WARP) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
@@ -541,7 +564,8 @@ static size_t psf_smem_bytes() { return SMEM_BYTES + 1024; }
 size_t psf_work_floats(int S, int ldm, bool symmetric) { return (size_t)S * 2 * ldm * (symmetric ? 2 : 4); }
 
 cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre, const float *Rim, int ldm, int M,
-                               int S, float scale, void *A, int lda, int a_dtype, float *work, cudaStream_t st) {
+                               int S, float scale, void *A, int lda, int a_dtype, float *work, int *status,
+                               unsigned long long timeout_ns, int hold, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     if (ldm % KC || !work) return cudaErrorInvalidValue;
     const bool symmetric = Lre == Rre && Lim == Rim;
@@ -577,18 +601,19 @@ cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre
     if (e != cudaSuccess) return e;
     const int grid = (int)(ntiles < sms ? ntiles : sms);
     const size_t smem = psf_smem_bytes();
-    const unsigned long long timeout_ns = 2000000000ull;
     if (a_dtype == DAMAS_BF16) {
         e = cudaFuncSetAttribute(psf_gram_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         psf_gram_tc_kernel<__nv_bfloat16><<<grid, THREADS, smem, st>>>(
-            maps, M, S, scale, (__nv_bfloat16 *)A, lda, symmetric ? 1 : 0, ntx, (int)ntiles, timeout_ns);
+            maps, M, S, scale, (__nv_bfloat16 *)A, lda, symmetric ? 1 : 0, ntx, (int)ntiles, timeout_ns, status,
+            hold);
     } else {
         e = cudaFuncSetAttribute(psf_gram_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         psf_gram_tc_kernel<float><<<grid, THREADS, smem, st>>>(maps, M, S, scale, (float *)A, lda,
-                                                               symmetric ? 1 : 0, ntx, (int)ntiles, timeout_ns);
+                                                               symmetric ? 1 : 0, ntx, (int)ntiles, timeout_ns,
+                                                               status, hold);
     }
     return cudaGetLastError();
 }

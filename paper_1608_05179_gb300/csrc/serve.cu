@@ -9,10 +9,14 @@
 //   stage 2: restriction of b, PSF matrix of every bin's kept points, one
 //            Gauss-Seidel launch for all the request's bins, power maps,
 //            download of the results.
-// A request enters stage 1 when a pool slot and its stage-1 memory fit the HBM
-// budget, and stage 2 when its matrices fit the budget and its solver CTAs fit
-// the free SM slots; so the cooperative solves in flight always fit on the
-// device together.  Requests that arrive while others run are admitted as
+// A request enters stage 1 when a pool slot is free and its stage-1 memory plus
+// the least its stage 2 can need fit the HBM budget beside the requests in
+// flight, and stage 2 when its matrices fit the budget and its solve's share of
+// the SMs fits the free half-SM units (the library's plan of that solve: a CTA
+// that fills an SM counts twice); so the cooperative solves in flight always
+// fit on the device together.  A request that does not fit even alone runs
+// when nothing else is in flight, and stage 2 is always granted when no other
+// request is solving, so a small budget slows the loop but never stalls it.  Requests that arrive while others run are admitted as
 // memory and slots free up, and their kernels overlap on the device.  Device
 // memory comes from the stream-ordered allocator of each request's stream.
 #include <math.h>
@@ -45,12 +49,12 @@ struct Job {
     double *h_tot = nullptr;
     int *h_Sf = nullptr;
     int *h_status = nullptr;
-    double t_submit = 0, t_admit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_solve = 0, t_done = 0;
     int status = DAMAS_EBUSY;
     int stage = 0;  // 0 queued, 1 stage 1 running, 2 waiting for stage 2, 3 stage 2 running, 4 done
     int slot = -1;
     size_t bytes1 = 0, bytes2 = 0;
-    int ctas = 0;
+    int units = 0;  // half-SM units its solve holds (solve_half_sm_units)
     std::vector<int> ctas_f;
     cudaEvent_t ev1 = nullptr, ev2 = nullptr;
     // device buffers
@@ -76,7 +80,7 @@ struct ServeState {
     std::vector<cudaStream_t> streams;
     std::vector<Job *> running;
     size_t held_bytes = 0;
-    int held_ctas = 0;
+    int held_units = 0;
 };
 
 namespace {
@@ -101,6 +105,21 @@ damas_geom job_geom(const Job &j) {
 size_t stage1_bytes(const damas_request &r) {
     const size_t S = (size_t)r.nx * r.ny, F = r.n_bins;
     return (size_t)r.M * 3 * 8 + F * r.M * r.M * 8 + F * S * 8 + F * 4 + 64;
+}
+
+// The least memory stage 2 can need, known before the compressed sizes: every
+// bin keeps at least G^0 (Algorithm 1) and, with a keep fraction f, at least
+// ceil(f S) points; a full-grid request keeps all S.  Same terms as plan_stage2.
+size_t stage2_bytes_lower(const damas_request &r) {
+    const size_t S = (size_t)r.nx * r.ny, F = r.n_bins;
+    size_t n = S;
+    if (r.wavelet.levels > 0) {
+        const int J = r.wavelet.levels;
+        n = (size_t)(((r.nx - 1) >> J) + 1) * (size_t)(((r.ny - 1) >> J) + 1);
+        if (r.wavelet.eps_mode == DAMAS_EPS_KEEP_FRAC) n = std::max(n, (size_t)ceil(r.wavelet.eps * (double)S));
+        n = std::min(n, S);
+    }
+    return S * F * 4 + F * 8 + 64 + F * (n * (size_t)damas_lda((int)n) * 4 + n * 16);
 }
 
 // Stage 1 on the job's stream: uploads, DAS maps, compressed grids, S_f download.
@@ -136,21 +155,30 @@ int launch_stage1(ServeState &st, Job &j) {
     return cudaGetLastError() == cudaSuccess ? DAMAS_OK : DAMAS_ECUDA;
 }
 
-// Memory and CTAs stage 2 needs, from the compressed sizes.
-void plan_stage2(const ServeState &st, Job &j) {
+// Memory stage 2 needs, from the compressed sizes, and the share of the SMs
+// its solve holds: the library's own plan of that solve (form, CTAs per system,
+// CTAs per SM), so a single-CTA solve, whose one CTA fills an SM, is charged the
+// whole SM.
+int plan_stage2(const ServeState &st, Job &j) {
     const damas_request &r = j.req;
     const size_t S = (size_t)r.nx * r.ny;
     const int rows = st.cfg.rows_per_cta > 0 ? st.cfg.rows_per_cta : 512;
     j.bytes2 = S * r.n_bins * 4 + (size_t)r.n_bins * 8 + 64;
-    j.ctas = 0;
     j.ctas_f.assign(r.n_bins, 1);
+    std::vector<damas_system> sys(r.n_bins);
     for (int f = 0; f < r.n_bins; ++f) {
         const size_t n = (size_t)j.h_Sf[f];
         j.bytes2 += n * (size_t)damas_lda((int)n) * 4 + n * 16;
         const int nb = (int)((n + 31) / 32);
         j.ctas_f[f] = std::max(1, std::min(nb, (int)((n + rows - 1) / rows)));
-        j.ctas += j.ctas_f[f];
+        memset(&sys[f], 0, sizeof(damas_system));
+        sys[f].a_dtype = DAMAS_F32;
+        sys[f].S = (int)n;
+        sys[f].lda = damas_lda((int)n);
+        sys[f].iters = r.iters;
+        sys[f].ctas = j.ctas_f[f];
     }
+    return solve_half_sm_units(st.pool[j.slot], sys.data(), r.n_bins, &j.units);
 }
 
 // Stage 2 on the job's stream: PSF matrices, one solve for all bins, power maps, downloads.
@@ -236,11 +264,16 @@ void free_device(ServeState &st, Job &j) {
 // A request ends (done or failed): free its device memory once its stream is
 // idle, return its memory, CTAs and pool slot, and publish the status.
 void complete(ServeState &st, Job &j, int status, std::vector<bool> &busy) {
-    if (status != DAMAS_OK) cudaStreamSynchronize(st.streams[j.slot]);
+    if (status != DAMAS_OK) {
+        // let the failed request's work finish, and clear a build status it left
+        // on the pool context so that the slot's next request starts clean
+        cudaStreamSynchronize(st.streams[j.slot]);
+        damas_check(st.pool[j.slot], st.streams[j.slot]);
+    }
     free_device(st, j);
     std::lock_guard<std::mutex> lk(st.mu);
     st.held_bytes -= j.bytes1 + j.bytes2;
-    st.held_ctas -= j.ctas;
+    st.held_units -= j.units;
     busy[j.slot] = false;
     j.status = status;
     j.stage = 4;
@@ -271,7 +304,10 @@ void worker_loop(ServeState *stp) {
                 if (slot < 0) break;
                 Job *q = st.queue.front();
                 const size_t b1 = stage1_bytes(q->req);
-                if (st.held_bytes + b1 > budget && !st.running.empty()) break;
+                // its stage 1 and the least its stage 2 can need must fit beside
+                // what the requests in flight hold (a request runs alone when it
+                // does not fit even so)
+                if (st.held_bytes + b1 + stage2_bytes_lower(q->req) > budget && !st.running.empty()) break;
                 st.queue.pop_front();
                 q->slot = slot;
                 q->bytes1 = b1;
@@ -293,24 +329,32 @@ void worker_loop(ServeState *stp) {
         }
         for (Job *j : run) {
             if (j->stage == 1 && cudaEventQuery(j->ev1) == cudaSuccess) {
-                plan_stage2(st, *j);
+                const int rc = plan_stage2(st, *j);
+                if (rc) {
+                    j->bytes2 = 0;  // nothing of stage 2 was charged
+                    j->units = 0;
+                    complete(st, *j, rc, busy);
+                    continue;
+                }
                 j->stage = 2;
                 progress = true;
             }
             if (j->stage == 2) {
-                // stage 2 needs its matrices within the budget and its solver CTAs
-                // within the free SM slots (always granted when nothing else runs it)
+                // stage 2 needs its matrices within the budget and its solver's
+                // share of the SMs within the free units (always granted when no
+                // other request is in stage 2)
                 bool go;
                 {
                     std::lock_guard<std::mutex> lk(st.mu);
                     int in_stage2 = 0;
                     for (Job *o : st.running) in_stage2 += o->stage == 3 ? 1 : 0;
                     go = in_stage2 == 0 ||
-                         (st.held_bytes + j->bytes2 <= budget && st.held_ctas + j->ctas <= slots);
+                         (st.held_bytes + j->bytes2 <= budget && st.held_units + j->units <= slots);
                     if (go) {
                         st.held_bytes += j->bytes2;
-                        st.held_ctas += j->ctas;
+                        st.held_units += j->units;
                         j->stage = 3;
+                        j->t_solve = now_s();
                     }
                 }
                 if (go) {
@@ -432,7 +476,10 @@ int damas_serve_poll(damas_ctx *ctx, uint64_t ticket, damas_result *res) {
     res->S = j.req.nx * j.req.ny;
     res->t_submit = j.t_submit;
     res->t_admit = j.t_admit;
+    res->t_solve = j.t_solve;
     res->t_done = j.t_done;
+    res->hbm_bytes = j.bytes1 + j.bytes2;
+    res->sm_units = j.units;
     if (j.stage == 4) {
         res->x = j.h_x;
         res->total_power = j.h_tot;

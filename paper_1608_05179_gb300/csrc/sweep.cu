@@ -780,12 +780,25 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
     if (warp == 0 && !RES) cp_async_wait_all();
 }
 
+// A build kernel of the context gave up a wait (so A may hold NaN): report it
+// and leave x and the state untouched.  Read by one thread and shared, so every
+// thread of the CTA takes the same branch.
+__device__ __forceinline__ bool upstream_failed(const SweepParams &p) {
+    __shared__ int s_up;
+    if (threadIdx.x == 0) s_up = p.upstream ? ld_volatile_i32(p.upstream) : 0;
+    __syncthreads();
+    if (s_up == 0) return false;
+    if (threadIdx.x == 0) atomicCAS(p.status, 0, (int)DAMAS_ETIMEDOUT);
+    return true;
+}
+
 __global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepParams p) {
     extern __shared__ __align__(16) char smem[];
     __shared__ float dring[4][32];
     __shared__ unsigned char nzidx[4][32];
     __shared__ int nzcnt[4];
     __shared__ int s_abort;
+    if (upstream_failed(p)) return;
     int si = 0;
     while (si + 1 < p.nsys && (int)blockIdx.x >= p.sys[si + 1].cta0) ++si;
     const SweepSys s = p.sys[si];
@@ -1285,6 +1298,7 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1)
     __shared__ int nzcnt[4];
     __shared__ __align__(8) unsigned long long tbar[SOLO_SLOTS];
     __shared__ int s_abort;
+    if (upstream_failed(p)) return;
     const SweepSys s = p.sys[blockIdx.x];
     if (s.dtype == DAMAS_F32)
         sweep_solo<true>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
@@ -1385,6 +1399,13 @@ bool make_sweep_tile_map(CUtensorMap *m, const void *At, int dtype, int lda, int
               const_cast<void *>(At), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
+}
+
+cudaError_t sweep_solo_occupancy(size_t smem, int *blocks_per_sm) {
+    cudaError_t e =
+        cudaFuncSetAttribute(damas_sweep_solo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, damas_sweep_solo_kernel, SOLO_THREADS, smem);
 }
 
 cudaError_t launch_sweep_solo(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st) {

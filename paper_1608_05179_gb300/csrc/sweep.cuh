@@ -24,6 +24,9 @@ struct SweepParams {
     int *status;
     unsigned long long timeout_ns;
     int withhold_block;  // test hook: block index never published, or -1
+    const int *upstream; // the context's build status word, or nullptr: when it holds an error at
+                         // launch (a build kernel gave up a wait, so A may hold NaN), the launch
+                         // reports DAMAS_ETIMEDOUT and leaves x unchanged
 };
 static_assert(sizeof(SweepParams) <= 32000, "kernel parameter block");
 
@@ -38,5 +41,6 @@ struct SoloMaps {
     CUtensorMap m[SWEEP_MAX_SYS];
 };
 size_t sweep_solo_smem_bytes(int R, int dtype);
+cudaError_t sweep_solo_occupancy(size_t smem, int *blocks_per_sm);
 bool make_sweep_tile_map(CUtensorMap *m, const void *At, int dtype, int lda, int S);
 cudaError_t launch_sweep_solo(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st);

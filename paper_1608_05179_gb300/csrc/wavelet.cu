@@ -305,7 +305,9 @@ extern "C" int wavelet_compress_grid_noalloc(damas_ctx *ctx, const float *b_dev,
     if (!ctx) return DAMAS_EINVAL;
     if (!cfg) return ctx_fail(ctx, DAMAS_EINVAL, "cfg is NULL");
     if (!b_dev || !idx_dev || !S_sub_dev) return ctx_fail(ctx, DAMAS_EINVAL, "b_dev, idx_dev, S_sub_dev are required");
-    if (nx < 1 || ny < 1 || (long long)nx * ny > DAMAS_NOALLOC_MAX_POINTS)
+    if (nx < 1 || ny < 1 || nx > 65535 || ny > 65535)
+        return ctx_fail(ctx, DAMAS_EINVAL, "grid %dx%d: nx and ny must be in 1..65535", nx, ny);
+    if ((long long)nx * ny > DAMAS_NOALLOC_MAX_POINTS)
         return ctx_fail(ctx, DAMAS_EINVAL, "grid %dx%d exceeds the %d points of the allocation-free work array", nx, ny,
                         DAMAS_NOALLOC_MAX_POINTS);
     if (cfg->levels < 1 || cfg->levels > 15) return ctx_fail(ctx, DAMAS_EINVAL, "levels=%d out of range", cfg->levels);

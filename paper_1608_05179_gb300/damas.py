@@ -105,6 +105,18 @@ class Geometry:
                         int(diag_removal))
 
 
+def damas_set_option(ctx: Context, option: int, value: int):
+    """Context option: _lib.OPT_BUILD_TIMEOUT_MS (bound on the build kernels'
+    device waits) or _lib.OPT_TEST_HOLD_BUILD (test hook of those waits)."""
+    ctx.check(ctx.lib.damas_set_option(ctx.handle, int(option), int(value)))
+
+
+def damas_check(ctx: Context, stream=None):
+    """Synchronise the stream; raise DamasError(DAMAS_ETIMEDOUT) when a build
+    kernel of the context gave up a bounded wait since the last check."""
+    ctx.check(ctx.lib.damas_check(ctx.handle, _stream(stream)))
+
+
 def damas_lda(S: int) -> int:
     return _lib.load().damas_lda(int(S))
 

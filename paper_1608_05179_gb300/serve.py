@@ -35,6 +35,9 @@ class Result:
     t_submit: float
     t_admit: float
     t_done: float
+    t_solve: float = 0.0      # stage-2 admission (matrices and solve)
+    hbm_bytes: int = 0        # device memory charged against the budget
+    sm_units: int = 0         # half-SM units charged to its solve
 
     @property
     def latency(self) -> float:
@@ -76,7 +79,8 @@ class Server:
         F, S = res.n_bins, res.S
         out = Result(np.ctypeslib.as_array(res.x, shape=(F * S,)).reshape(F, S).copy(),
                      np.ctypeslib.as_array(res.total_power, shape=(F,)).copy(),
-                     np.ctypeslib.as_array(res.S_sub, shape=(F,)).copy(), res.t_submit, res.t_admit, res.t_done)
+                     np.ctypeslib.as_array(res.S_sub, shape=(F,)).copy(), res.t_submit, res.t_admit, res.t_done,
+                     res.t_solve, int(res.hbm_bytes), int(res.sm_units))
         self.ctx.check(self.ctx.lib.damas_serve_release(self.ctx.handle, ctypes.c_uint64(ticket)))
         return out
 

@@ -47,6 +47,8 @@ def test_struct_layouts_match_c():
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(damas_geom), sizeof(damas_wavelet_cfg), sizeof(damas_system), sizeof(damas_solve_cfg));
   printf("%zu %zu %zu %zu\n", offsetof(damas_geom, formulation), offsetof(damas_system, ctas), offsetof(damas_solve_cfg, a_placement), offsetof(damas_geom, diag_removal));
+  printf("%zu %zu %zu %zu\n", sizeof(damas_result), offsetof(damas_result, t_solve), offsetof(damas_result, hbm_bytes), offsetof(damas_result, sm_units));
+  printf("%zu %zu %zu\n", sizeof(damas_request), sizeof(damas_serve_cfg), offsetof(damas_request, iters));
   return 0;
 }
 """
@@ -55,13 +57,17 @@ int main(void) {
         open(c, "w").write(src)
         exe = os.path.join(d, "t")
         subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
-        l1, l2 = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+        l1, l2, l3, l4 = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
     sizes = [int(v) for v in l1.split()]
     offs = [int(v) for v in l2.split()]
     assert sizes == [ctypes.sizeof(_lib.damas_geom), ctypes.sizeof(_lib.damas_wavelet_cfg),
                      ctypes.sizeof(_lib.damas_system), ctypes.sizeof(_lib.damas_solve_cfg)]
     assert offs == [_lib.damas_geom.formulation.offset, _lib.damas_system.ctas.offset,
                     _lib.damas_solve_cfg.a_placement.offset, _lib.damas_geom.diag_removal.offset]
+    assert [int(v) for v in l3.split()] == [ctypes.sizeof(_lib.damas_result), _lib.damas_result.t_solve.offset,
+                                            _lib.damas_result.hbm_bytes.offset, _lib.damas_result.sm_units.offset]
+    assert [int(v) for v in l4.split()] == [ctypes.sizeof(_lib.damas_request), ctypes.sizeof(_lib.damas_serve_cfg),
+                                            _lib.damas_request.iters.offset]
 
 
 def test_host_only_entry_points(lib):

@@ -76,3 +76,20 @@ def test_noalloc_rejects_grids_beyond_its_work_array(ctx):
                                            None, None, None)
     assert rc == _lib.DAMAS_EINVAL
     assert b"allocation-free" in lib.damas_last_error(ctx.handle)
+
+
+def test_noalloc_has_the_limits_of_the_context_entry_point(ctx):
+    """A 262144 x 1 grid fits the work array, but a side above 65535 is refused by
+    both entry points alike."""
+    from paper_1608_05179_gb300 import _lib
+    lib = _lib.load()
+    nx, ny = 262144, 1
+    b = torch.zeros(nx * ny, device="cuda")
+    idx = torch.empty(nx * ny, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int32, device="cuda")
+    cfg = _lib.damas_wavelet_cfg(1, D.PRED_LINEAR, D.EPS_ABS, 0.1)
+    args = (ctx.handle, ctypes.c_void_p(b.data_ptr()), nx, ny, ctypes.byref(cfg), ctypes.c_void_p(idx.data_ptr()),
+            ctypes.c_void_p(cnt.data_ptr()), None, None, None)
+    assert lib.wavelet_compress_grid(*args) == _lib.DAMAS_EINVAL
+    assert lib.wavelet_compress_grid_noalloc(*args) == _lib.DAMAS_EINVAL
+    assert b"65535" in lib.damas_last_error(ctx.handle)
