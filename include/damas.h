@@ -392,6 +392,34 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
                 damas_stream stream);
 
 /*
+ * Mixed-precision schedule of the iteration (the precision study's form): for
+ * each system, iters_bulk sweeps of Eq. (13)-(14) with A stored in BF16 (half
+ * the bytes of A per sweep) from x^0 = 0, then iters_refine sweeps with A in
+ * FP32 that restart from the exact FP32 residual A x - b of the bulk phase's x
+ * (DAMAS_INIT_X), in one call.  iters_bulk = 0 solves with the FP32 A from
+ * x^0 = 0; iters_refine = 0 stops after the bulk phase.  The result is bit for
+ * bit that of the two damas_solve calls it stands for.
+ *   A_bulk_dev / At_bulk_dev     BF16 A and its transpose (NULL: A symmetric)
+ *   A_refine_dev / At_refine_dev FP32 A and its transpose (NULL: A symmetric)
+ *   lda                          row stride of both, in elements (a multiple of 32)
+ * cfg and the status follow damas_solve: the status reports the first wait that
+ * ran out in either phase (withhold_block must be 0).  The two phases run as
+ * two launches on the stream; without cfg->status_dev the call synchronises
+ * once, at the end.
+ */
+typedef struct {
+    const void *A_bulk_dev, *At_bulk_dev;
+    const void *A_refine_dev, *At_refine_dev;
+    int lda, S;
+    const float *b_dev; /* device float[S] */
+    float *x_dev;       /* device float[S], output */
+    int iters_bulk, iters_refine;
+    int ctas;           /* as damas_system.ctas */
+} damas_mixed_system;
+int damas_solve_mixed(damas_ctx *ctx, const damas_mixed_system *sys, int nsys, const damas_solve_cfg *cfg,
+                      damas_stream stream);
+
+/*
  * The plan damas_solve would choose for one system of S rows when it is the
  * only system of the call (host only; no device work): CTAs in its team, rows
  * per CTA, and whether the CTAs keep their rows of A in shared memory (1) or

@@ -41,6 +41,12 @@ class damas_solve_cfg(ctypes.Structure):
                 ("a_placement", c_int), ("withhold_block", c_int)]
 
 
+class damas_mixed_system(ctypes.Structure):
+    _fields_ = [("A_bulk_dev", c_void_p), ("At_bulk_dev", c_void_p), ("A_refine_dev", c_void_p),
+                ("At_refine_dev", c_void_p), ("lda", c_int), ("S", c_int), ("b_dev", c_void_p), ("x_dev", c_void_p),
+                ("iters_bulk", c_int), ("iters_refine", c_int), ("ctas", c_int)]
+
+
 class damas_serve_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", c_int), ("sm_slots", c_int),
                 ("rows_per_cta", c_int)]
@@ -86,6 +92,8 @@ SIGNATURES = {
     "damas_scatter_power": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
                                     c_void_p]),
     "damas_solve": (c_int, [c_void_p, ctypes.POINTER(damas_system), c_int, ctypes.POINTER(damas_solve_cfg), c_void_p]),
+    "damas_solve_mixed": (c_int, [c_void_p, ctypes.POINTER(damas_mixed_system), c_int,
+                                  ctypes.POINTER(damas_solve_cfg), c_void_p]),
     "damas_solve_plan": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "damas_handover_probe": (c_int, [c_void_p, c_int, c_int, c_int, ctypes.POINTER(ctypes.c_double),

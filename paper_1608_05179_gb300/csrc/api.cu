@@ -601,10 +601,11 @@ int damas_handover_probe(damas_ctx *ctx, int rounds, int max_pairs, int timeout_
     return DAMAS_OK;
 }
 
-int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg, damas_stream stream) {
-    if (!ctx) return DAMAS_EINVAL;
-    if (nsys < 0 || (nsys > 0 && !sys)) return ctx_fail(ctx, DAMAS_EINVAL, "bad system array");
-    if (nsys == 0) return DAMAS_OK;
+}  // extern "C"
+
+namespace {
+
+int check_systems(damas_ctx *ctx, const damas_system *sys, int nsys) {
     for (int i = 0; i < nsys; ++i) {
         const damas_system &s = sys[i];
         if (s.S < 1) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: S=%d", i, s.S);
@@ -619,12 +620,18 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         if (s.iters < 0 || s.iters > (1 << 24)) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: iters=%d", i, s.iters);
         if (s.ctas < 0) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: ctas=%d", i, s.ctas);
     }
+    return DAMAS_OK;
+}
+
+// The body of damas_solve on validated systems.  clear_status: start the call's
+// status word at DAMAS_OK (a later call of a sequence keeps an earlier error);
+// finish: without cfg->status_dev, synchronise and return the status.
+int solve_checked(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg, cudaStream_t st,
+                  bool clear_status, bool finish) {
     const int forced = cfg ? cfg->ctas_per_system : 0;
     const int placement = cfg ? cfg->a_placement : 0;
     if (placement < 0 || placement > 2) return ctx_fail(ctx, DAMAS_EINVAL, "a_placement=%d", placement);
     const long long timeout_ms = (cfg && cfg->timeout_ms > 0) ? cfg->timeout_ms : 2000;
-    DeviceGuard dg(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
 
     std::vector<Plan> plans;
     std::vector<Launch> launches;
@@ -649,7 +656,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
     rc = ctx_ensure(ctx, ctx->status, 64);
     if (rc) return rc;
     int *status = cfg && cfg->status_dev ? cfg->status_dev : (int *)ctx->status.ptr;
-    DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+    if (clear_status) DAMAS_CUDA_TRY(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
 
     // A launch recorded into a CUDA graph keeps the epoch it was recorded with, so
     // every replay would find the words of the previous replay already "new": the
@@ -712,7 +719,7 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
         }
         ctx->epoch += (unsigned)L.max_iters + 1u;
     }
-    if (cfg && cfg->status_dev) return DAMAS_OK;
+    if (!finish || (cfg && cfg->status_dev)) return DAMAS_OK;
     int h = 0;
     DAMAS_CUDA_TRY(ctx, cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     DAMAS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -721,6 +728,70 @@ int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_s
                         "a device wait ran out: in the solve (limit %lld ms), or in a build kernel of this context "
                         "before it (damas_check reports and clears that)",
                         timeout_ms);
+    return DAMAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int damas_solve(damas_ctx *ctx, const damas_system *sys, int nsys, const damas_solve_cfg *cfg, damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (nsys < 0 || (nsys > 0 && !sys)) return ctx_fail(ctx, DAMAS_EINVAL, "bad system array");
+    if (nsys == 0) return DAMAS_OK;
+    int rc = check_systems(ctx, sys, nsys);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    return solve_checked(ctx, sys, nsys, cfg, (cudaStream_t)stream, true, true);
+}
+
+int damas_solve_mixed(damas_ctx *ctx, const damas_mixed_system *msys, int nsys, const damas_solve_cfg *cfg,
+                      damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (nsys < 0 || (nsys > 0 && !msys)) return ctx_fail(ctx, DAMAS_EINVAL, "bad system array");
+    if (nsys == 0) return DAMAS_OK;
+    if (cfg && cfg->withhold_block) return ctx_fail(ctx, DAMAS_EINVAL, "withhold_block is a damas_solve test hook");
+    // the two phases as plain systems: BF16 from x = 0, then FP32 from the exact
+    // residual of the bulk phase's x (or from x = 0 when there is no bulk phase)
+    std::vector<damas_system> bulk, refine;
+    for (int i = 0; i < nsys; ++i) {
+        const damas_mixed_system &m = msys[i];
+        if (m.iters_bulk < 0 || m.iters_refine < 0)
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: negative sweep count", i);
+        damas_system s;
+        memset(&s, 0, sizeof(s));
+        s.lda = m.lda;
+        s.S = m.S;
+        s.b_dev = m.b_dev;
+        s.x_dev = m.x_dev;
+        s.ctas = m.ctas;
+        if (m.iters_bulk > 0) {
+            s.A_dev = m.A_bulk_dev;
+            s.At_dev = m.At_bulk_dev;
+            s.a_dtype = DAMAS_BF16;
+            s.init = DAMAS_INIT_ZERO;
+            s.iters = m.iters_bulk;
+            bulk.push_back(s);
+        }
+        if (m.iters_refine > 0 || m.iters_bulk == 0) {
+            s.A_dev = m.A_refine_dev;
+            s.At_dev = m.At_refine_dev;
+            s.a_dtype = DAMAS_F32;
+            s.init = m.iters_bulk > 0 ? DAMAS_INIT_X : DAMAS_INIT_ZERO;
+            s.iters = m.iters_refine;
+            refine.push_back(s);
+        }
+    }
+    int rc = check_systems(ctx, bulk.data(), (int)bulk.size());
+    if (rc == DAMAS_OK) rc = check_systems(ctx, refine.data(), (int)refine.size());
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!bulk.empty()) {
+        rc = solve_checked(ctx, bulk.data(), (int)bulk.size(), cfg, st, true, refine.empty());
+        if (rc) return rc;
+    }
+    if (!refine.empty()) return solve_checked(ctx, refine.data(), (int)refine.size(), cfg, st, bulk.empty(), true);
     return DAMAS_OK;
 }
 

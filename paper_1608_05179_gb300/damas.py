@@ -322,15 +322,22 @@ def damas_handover_probe(ctx: Context, rounds: int = 100, max_pairs: int = 1 << 
 
 
 def solve_mixed(ctx: Context, A_bf16: torch.Tensor, A_f32: torch.Tensor, b: torch.Tensor, x: torch.Tensor,
-                iters_bulk: int, iters_refine: int, stream=None, **kw):
-    """Mixed-precision schedule: iters_bulk sweeps with A stored in BF16 (half the
-    bytes per sweep), then iters_refine sweeps with the FP32 A, which restart from
+                iters_bulk: int, iters_refine: int, At_bf16: torch.Tensor | None = None,
+                At_f32: torch.Tensor | None = None, ctas: int = 0, ctas_per_system: int = 0, timeout_ms: int = 0,
+                status: torch.Tensor | None = None, a_placement: int = PLACE_AUTO, stream=None):
+    """Mixed-precision schedule in one C call (damas_solve_mixed): iters_bulk sweeps
+    with A stored in BF16 from x = 0, then iters_refine sweeps with the FP32 A from
     the exact FP32 residual of the current x."""
-    if iters_bulk:
-        damas_solve(ctx, System(A_bf16, b, x, iters_bulk, init=INIT_ZERO), stream=stream, **kw)
-    if iters_refine:
-        damas_solve(ctx, System(A_f32, b, x, iters_refine, init=INIT_X if iters_bulk else INIT_ZERO),
-                    stream=stream, **kw)
+    if A_bf16.dtype != torch.bfloat16 or A_f32.dtype != torch.float32 or A_bf16.shape != A_f32.shape:
+        raise ValueError("A_bf16 (bfloat16) and A_f32 (float32) of one shape are required")
+    S = int(b.numel())
+    m = _lib.damas_mixed_system(A_bf16.data_ptr(), At_bf16.data_ptr() if At_bf16 is not None else None,
+                                A_f32.data_ptr(), At_f32.data_ptr() if At_f32 is not None else None,
+                                int(A_f32.shape[1]), S, b.data_ptr(), x.data_ptr(), int(iters_bulk),
+                                int(iters_refine), int(ctas))
+    cfg = _lib.damas_solve_cfg(int(ctas_per_system), int(timeout_ms),
+                               status.data_ptr() if status is not None else None, int(a_placement), 0)
+    ctx.check(ctx.lib.damas_solve_mixed(ctx.handle, ctypes.byref(m), 1, ctypes.byref(cfg), _stream(stream)))
     return x
 
 

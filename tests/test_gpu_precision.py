@@ -61,3 +61,45 @@ def test_bf16_bulk_with_fp32_refinement_per_source_db(ctx):
     assert err["fp32"].max() <= 0.05, err["fp32"]
     assert err["bf16+fp32"].max() <= 0.5, err["bf16+fp32"]
     assert err["bf16+fp32"].max() <= err["bf16"].max() + 1e-6
+
+
+def _padded(A64, dtype):
+    S = A64.shape[0]
+    out = np.zeros((S, D.damas_lda(S)), np.float32)
+    out[:, :S] = A64
+    return torch.as_tensor(out, device="cuda").to(dtype)
+
+
+@pytest.mark.parametrize("nb,nr", [(300, 50), (0, 120), (200, 0)])
+def test_solve_mixed_in_one_call_equals_the_two_solves(ctx, nb, nr):
+    """damas_solve_mixed through the C ABI, two systems in one call, against the
+    two damas_solve calls it stands for (BF16 from zero, then FP32 from the
+    exact residual): bit for bit."""
+    import ctypes
+    from paper_1608_05179_gb300 import _lib
+    lib = _lib.load()
+    systems = [synth.random_psd_system(np.random.default_rng(s), S) for s, S in ((1, 300), (2, 701))]
+    ms, xs, refs = [], [], []
+    for A64, b64 in systems:
+        A32, Abf = _padded(A64, torch.float32), _padded(A64, torch.bfloat16)
+        b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+        x = torch.full((len(b64),), 3.0, device="cuda")
+        ms.append(_lib.damas_mixed_system(Abf.data_ptr(), None, A32.data_ptr(), None, A32.shape[1], len(b64),
+                                          b.data_ptr(), x.data_ptr(), nb, nr, 0))
+        xs.append((x, A32, Abf, b))
+        xr = torch.zeros(len(b64), device="cuda")
+        if nb:
+            D.damas_solve(ctx, D.System(Abf, b, xr, nb, init=D.INIT_ZERO))
+        if nr or not nb:
+            D.damas_solve(ctx, D.System(A32, b, xr, nr, init=D.INIT_X if nb else D.INIT_ZERO))
+        refs.append(xr)
+    arr = (_lib.damas_mixed_system * 2)(*ms)
+    rc = lib.damas_solve_mixed(ctx.handle, arr, 2, None, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.damas_last_error(ctx.handle)
+    for (x, *_), xr in zip(xs, refs):
+        assert torch.equal(x, xr)
+    # the binding (one system) gives the same
+    x, A32, Abf, b = xs[0]
+    x2 = torch.zeros_like(x)
+    D.solve_mixed(ctx, Abf, A32, b, x2, nb, nr)
+    assert torch.equal(x2, refs[0])
