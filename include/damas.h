@@ -148,9 +148,10 @@ int damas_state_floats(int S);
  *             padding columns S_sub..lda-1 are written as 0.
  *   gnorm2_dev optional device float[S_sub]: ||g_n||^2 of the selected points
  *             (formulation E uses it to turn x' into power).
- * Steering and propagation vectors are formed with the phase k*d in FP64,
- * reduced to a fraction of a period before an FP32 sine/cosine; the complex
- * Gram products accumulate in FP32.  The Gram's device waits are bounded
+ * Steering and propagation vectors are formed with the distance and the phase
+ * k*d in FP64, reduced to a fraction of a period before an FP32 sine/cosine;
+ * amplitudes and ||g||^2 are FP32 (the latter a compensated sum); the complex
+ * Gram products accumulate in FP32.  FP64 serves the phase argument only.  The Gram's device waits are bounded
  * (DAMAS_OPT_BUILD_TIMEOUT_MS); one that runs out is reported by damas_check
  * and by the next damas_solve on the context, not by this call.
  */
@@ -207,8 +208,9 @@ int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float 
  *   C_dev     device float[F][M][M][2] output, interleaved (re, im), exactly Hermitian.
  * Limits: M 1..DAMAS_MAX_MICS, K 2..1048576, hop >= 1, F 1..4096, M * L <= 4194240.
  * The DFT of the selected bins runs as a tiled product of the sample blocks
- * with a window-and-twiddle table (angles reduced exactly in integers, sine and
- * cosine in FP64); products and sums in FP32.
+ * with a window-and-twiddle table (angles reduced exactly in integers to a
+ * fraction of a period in [-1/2, 1/2], FP32 sine and cosine); products and sums
+ * in FP32.
  */
 int damas_csm(damas_ctx *ctx, const float *p_dev, int M, long long T, int K, int hop, const int32_t *bins_dev,
               int F, float *C_dev, damas_stream stream);
@@ -307,7 +309,8 @@ int damas_gather(damas_ctx *ctx, const float *src_dev, const int32_t *idx_dev, i
  *   x_full[idx[i]] = x_sub[i]               (gnorm2_dev NULL)
  * every other entry of x_full[S] is set to 0.  idx_dev NULL means the identity
  * (n == S).  total_power_dev (optional, device double[1]) receives the
- * integrated power sum_n x_full[n] (Table 1), summed in FP64 in a fixed order.
+ * integrated power sum_n x_full[n] (Table 1): a compensated FP32 sum in a fixed
+ * order, returned exactly as the double value of its (hi, lo) pair.
  */
 int damas_scatter_power(damas_ctx *ctx, const float *x_sub_dev, const int32_t *idx_dev, const float *gnorm2_dev,
                         int n, float *x_full_dev, int S, double *total_power_dev, damas_stream stream);
@@ -372,8 +375,8 @@ typedef struct {
  *   cfg    optional (NULL = defaults).
  * A system runs in one of two forms with bit-identical results (x and state):
  *  - single CTA: one CTA of 512 threads holds the whole system's x and
- *    residual, reads A from global memory (tiles by TMA, fold entries by
- *    asynchronous copies a step ahead) and hands nothing to other CTAs.  Used
+ *    residual, reads A from global memory (tiles a few steps ahead by TMA, the
+ *    entries of each fold as vector loads) and hands nothing to other CTAs.  Used
  *    for a system of 97 or more rows whose rows fit the CTA's shared memory
  *    when it is asked for one CTA (ctas = 1) with a_placement 0 or 2, or, by
  *    default, when it has at most 1024 rows; and only when every system of the

@@ -792,7 +792,9 @@ __device__ __forceinline__ bool upstream_failed(const SweepParams &p) {
     return true;
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepParams p) {
+// At most 128 registers a thread, so that two CTAs of streamed teams fit on an SM
+// (a batch of teams then runs side by side in one launch).
+__global__ void __launch_bounds__(SW_THREADS, 2) damas_sweep_kernel(const SweepParams p) {
     extern __shared__ __align__(16) char smem[];
     __shared__ float dring[4][32];
     __shared__ unsigned char nzidx[4][32];
@@ -828,11 +830,11 @@ __global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepP
 //  - the helper warp (1) folds dx_{G-2} and then dx_{G-1} into the rows of
 //    block J+1 from those tiles, so that block is current through dx_{G-1} when
 //    warp 0 solves it in step G+1 (adding dx_G itself, as in the team form);
-//  - the updater warps (all but 0, 1, 4, 8 and 12) issue, in step G,
-//    asynchronous copies of the entries of A that dx_{G-1} needs for their own
-//    rows (the first SOLO_STAGE nonzero columns) into a staging buffer, and fold
-//    dx_{G-2} from the buffer filled in step G-1 into every row but those of
-//    blocks J and J+1: the loads of a fold are in flight for a whole step.
+//  - the updater warps (all but 0, 1, 4, 8 and 12) fold dx_{G-2} into every
+//    row but those of blocks J and J+1, four rows per thread, reading the
+//    entries of A from global memory (L2) as one vector per column and group
+//    (staging them into shared memory a step ahead with asynchronous copies
+//    measured slower: 17.5 against 16.8 ms on the compressed 81x81 system).
 //    The last of them also forms the bound of block J-1 from that block's
 //    diagonal tile (its own rows start at 1280, so it is otherwise idle on
 //    compressed grids);
@@ -843,7 +845,6 @@ __global__ void __launch_bounds__(SW_THREADS, 1) damas_sweep_kernel(const SweepP
 // the end and the state a call starts from.
 constexpr int SOLO_SLOTS = 6;          // tile slots; the slot of step G+SOLO_PD is refilled in step G
 constexpr int SOLO_PD = 4;             // (slots G-1 and G are read in step G: SOLO_SLOTS >= SOLO_PD + 2)
-constexpr int SOLO_STAGE = 8;          // staged columns per dx (further nonzero columns are read directly)
 constexpr int SOLO_THREADS = 512;      // 16 warps
 constexpr int SOLO_UPD_THREADS = 352;  // the updaters: every warp but 0, 1, 4, 8 and 12
 static_assert(SOLO_SLOTS >= SOLO_PD + 2, "a slot must not be refilled while it is read");
@@ -851,10 +852,6 @@ static_assert(SOLO_SLOTS >= SOLO_PD + 2, "a slot must not be refilled while it i
 __device__ __forceinline__ bool solo_updater(int warp) { return warp >= 2 && (warp & 3) != 0; }
 __device__ __forceinline__ int solo_upd_index(int warp) { return warp - 2 - (warp >> 2); }
 
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
-}
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void solo_mbar_init(uint32_t bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -986,73 +983,40 @@ __device__ __forceinline__ void solo_tile_bound(const Team &T, const char *tdiag
     if (valid) bnd[r] = b;
 }
 
-// Updater thread ut: copy At[c0 + idx[u]][4g .. 4g+3] for its groups g of four
-// rows (blocks e1 and e2 left out) and the first SOLO_STAGE listed columns into
-// stage[u][4g ..]; always commits one group.
-template <bool F32>
-__device__ __forceinline__ void solo_stage(const SweepSys &s, const Team &T, char *stage, int ut, int c0,
-                                           const unsigned char *idx, int n, int e1, int e2) {
-    const int ns = n < SOLO_STAGE ? n : SOLO_STAGE;
-    const int elt = F32 ? 4 : 2;
-    const size_t col_bytes = (size_t)T.R * elt;
-    if (ns > 0)
-        for (int g = ut; 4 * g < T.S; g += SOLO_UPD_THREADS) {
-            const int blk = g >> 3;
-            if (blk == e1 || blk == e2) continue;
-            for (int u = 0; u < ns; ++u) {
-                const char *src = (const char *)s.At + ((size_t)(c0 + idx[u]) * s.lda + 4 * g) * elt;
-                char *dst = stage + u * col_bytes + (size_t)4 * g * elt;
-                if (F32)
-                    cp_async16(dst, src);
-                else
-                    cp_async8(dst, src);
-            }
-        }
-    cp_async_commit();
-}
-
 // Updater thread ut: fold the listed dx (columns c0 + idx[u]) into the rows of
-// its groups: every block but skip1 and skip2, or only block `only` when it is
-// >= 0.  Entries come from `stage` (filled by solo_stage with blocks nost1 and
-// nost2 left out) for the first SOLO_STAGE columns, else from global memory.
-// Each row's sum is formed exactly as by dot_list.
+// its groups of four: every block but skip1 and skip2, or only block `only`
+// when it is >= 0.  The entries of a column over a group are one 16-byte
+// (FP32) or 8-byte (BF16) load from global memory, two columns' loads issued
+// together.  Each row's sum is formed exactly as by dot_list.
 template <bool F32>
-__device__ __forceinline__ void solo_consume(const SweepSys &s, const Team &T, const char *stage, int ut, int c0,
-                                             const float *d, const unsigned char *idx, int n, int skip1, int skip2,
-                                             int only, int nost1, int nost2, float *rh, float *rl) {
+__device__ __forceinline__ void solo_fold(const SweepSys &s, const Team &T, int ut, int c0, const float *d,
+                                          const unsigned char *idx, int n, int skip1, int skip2, int only, float *rh,
+                                          float *rl) {
     if (n == 0) return;
-    const int elt = F32 ? 4 : 2;
-    const size_t col_bytes = (size_t)T.R * elt;
     for (int g = ut; 4 * g < T.S; g += SOLO_UPD_THREADS) {
         const int blk = g >> 3;
         if (only >= 0 ? blk != only : (blk == skip1 || blk == skip2)) continue;
-        const bool staged = stage != nullptr && blk != nost1 && blk != nost2;
         float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int u0 = 0; u0 < n; u0 += 2) {  // two columns at a time, their loads together
+        for (int u0 = 0; u0 < n; u0 += 2) {
             float a[2][4], dd[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
                 const int u = u0 + v < n ? u0 + v : u0;
                 const int c = idx[u];
                 dd[v] = d[c];
-                if (staged && u < SOLO_STAGE) {
-                    const char *p = stage + u * col_bytes + (size_t)4 * g * elt;
-                    if (F32) {
-                        const float4 w = *(const float4 *)p;
-                        a[v][0] = w.x;
-                        a[v][1] = w.y;
-                        a[v][2] = w.z;
-                        a[v][3] = w.w;
-                    } else {
-                        const uint2 w = *(const uint2 *)p;
-                        a[v][0] = bf16_lo(w.x);
-                        a[v][1] = bf16_hi(w.x);
-                        a[v][2] = bf16_lo(w.y);
-                        a[v][3] = bf16_hi(w.y);
-                    }
+                const size_t o = (size_t)(c0 + c) * s.lda + 4 * g;
+                if (F32) {
+                    const float4 w = *(const float4 *)((const float *)s.At + o);
+                    a[v][0] = w.x;
+                    a[v][1] = w.y;
+                    a[v][2] = w.z;
+                    a[v][3] = w.w;
                 } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) a[v][q] = col_at<F32>(s, c0 + c, 4 * g + q);
+                    const uint2 w = *(const uint2 *)((const unsigned short *)s.At + o);
+                    a[v][0] = bf16_lo(w.x);
+                    a[v][1] = bf16_hi(w.x);
+                    a[v][2] = bf16_lo(w.y);
+                    a[v][3] = bf16_hi(w.y);
                 }
             }
 #pragma unroll
@@ -1106,15 +1070,13 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
     const bool upd = solo_updater(warp);
     const int ut = upd ? solo_upd_index(warp) * 32 + lane : 0;
 
-    // tile slots first, 128-byte aligned for TMA; then rows and staging
+    // tile slots first, 128-byte aligned for TMA; then the rows
     char *tiles = smem + ((128u - (smem_addr(smem) & 127u)) & 127u);
     const int slot_bytes = 4 * 32 * T.tile_ld;
     float *rh = (float *)(tiles + SOLO_SLOTS * slot_bytes);
     float *rl = rh + R;
     float *xs = rl + R;
     float *bnd = xs + R;
-    char *stage = (char *)(bnd + R);
-    const size_t stage_bytes = (size_t)SOLO_STAGE * R * elt;
 
     // ---- prologue (as in the team form)
     if (threadIdx.x == 0) {
@@ -1203,7 +1165,6 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
         const int Jm1 = J == 0 ? nb - 1 : J - 1;
         const int Jm2 = Jm1 == 0 ? nb - 1 : Jm1 - 1;
         const int Jp1 = J + 1 == nb ? 0 : J + 1;
-        const int Jp2 = Jp1 + 1 == nb ? 0 : Jp1 + 1;
         const int gi = (int)(G & 3), g1 = (gi + 3) & 3, g2 = (gi + 2) & 3;
         const char *slot = tiles + sl * slot_bytes;
         if (warp == 0) {
@@ -1232,14 +1193,10 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
                 }
             }
         } else if (upd) {
-            solo_stage<F32>(s, T, stage + (G & 1) * stage_bytes, ut, Jm1 * 32, nzidx[g1], nzcnt[g1], Jp1, Jp2);
-            cp_async_wait_group<1>();  // the copies of step G-1
             if (G == 0)  // a resumed state holds dx_{-2} everywhere but in block nb-1
-                solo_consume<F32>(s, T, nullptr, ut, Jm2 * 32, dring[g2], nzidx[g2], nzcnt[g2], -1, -1, Jm1, -1, -1, rh,
-                                  rl);
+                solo_fold<F32>(s, T, ut, Jm2 * 32, dring[g2], nzidx[g2], nzcnt[g2], -1, -1, Jm1, rh, rl);
             else
-                solo_consume<F32>(s, T, stage + ((G - 1) & 1) * stage_bytes, ut, Jm2 * 32, dring[g2], nzidx[g2],
-                                  nzcnt[g2], J, Jp1, -1, J, Jp1, rh, rl);
+                solo_fold<F32>(s, T, ut, Jm2 * 32, dring[g2], nzidx[g2], nzcnt[g2], J, Jp1, -1, rh, rl);
             // the last updater warp (whose rows start at 1280): block J-1 was solved
             // in the previous step, its bound for the next solve
             if (warp == SOLO_THREADS / 32 - 1 && G > 0)
@@ -1260,7 +1217,6 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
                 const int sq = (int)(q % SOLO_SLOTS);
                 if (solo_mbar_wait(smem_addr(&tbar[sq]), (phase >> sq) & 1u, p.timeout_ns)) phase ^= 1u << sq;
             }
-        cp_async_wait_all();
         __syncthreads();
         return;
     }
@@ -1268,10 +1224,8 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
     // ---- drain to the team form's final state: dx_{Gend-2} into every block
     // but 0 (the helper's) and nb-1 (which the team form also leaves without it)
     if (Gend > 0 && upd) {
-        cp_async_wait_all();
         const int gq = (int)((Gend - 2) & 3);
-        solo_consume<F32>(s, T, stage + ((Gend - 1) & 1) * stage_bytes, ut, (nb - 2) * 32, dring[gq], nzidx[gq],
-                          nzcnt[gq], 0, nb - 1, -1, 0, 1, rh, rl);
+        solo_fold<F32>(s, T, ut, (nb - 2) * 32, dring[gq], nzidx[gq], nzcnt[gq], 0, nb - 1, -1, rh, rl);
     }
     __syncthreads();
 
@@ -1287,7 +1241,6 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
         const long long Gx = Gend - 2 + (threadIdx.x >> 5);
         s.state[2 * S + threadIdx.x] = dring[Gx & 3][lane];
     }
-    cp_async_wait_all();
 }
 
 __global__ void __launch_bounds__(SOLO_THREADS, 1)
@@ -1369,8 +1322,7 @@ cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream
 
 size_t sweep_solo_smem_bytes(int R, int dtype) {
     const size_t elt = dtype == DAMAS_F32 ? 4 : 2;
-    return 128 + (size_t)SOLO_SLOTS * 4 * 32 * 32 * elt + (size_t)4 * R * sizeof(float) +
-           (size_t)2 * SOLO_STAGE * R * elt;
+    return 128 + (size_t)SOLO_SLOTS * 4 * 32 * 32 * elt + (size_t)4 * R * sizeof(float);
 }
 
 // Tensor map over a system's At for the single-CTA form (FP32 or BF16, S rows of
