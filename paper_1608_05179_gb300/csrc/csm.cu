@@ -6,7 +6,8 @@
 //
 // csm_twiddle_kernel: the table tw[t][2f] = w(t) cos, tw[t][2f+1] = -w(t) sin of
 // the angle 2 pi ((bin_f * t) mod K) / K, the product reduced exactly in
-// integers before an FP64 sine/cosine of pi times the fraction.
+// integers to a fraction of a period in [-1/2, 1/2] before an FP32 sine/cosine
+// of pi times twice that fraction.
 // csm_dft_kernel: X = blocks x table as a real product - rows are (block,
 // microphone) pairs read straight from the overlapping blocks of p, columns
 // are (bin, re/im) - 64 x 64 tiles on CUDA cores, FP32 accumulation, X stored
@@ -23,12 +24,17 @@ __global__ void csm_twiddle_kernel(const int32_t *__restrict__ bins, int F, int 
     if (e >= (long long)K * F) return;
     const int t = (int)(e / F), f = (int)(e % F);
     const long long b = ((long long)bins[f] % K + K) % K;
-    const long long r = (b * t) % K;  // exact: angle = 2 pi r / K
-    double s, c;
-    sincospi(2.0 * (double)r / (double)K, &s, &c);
-    const double w = 0.5 - 0.5 * cospi(2.0 * (double)t / (double)K);
-    tw[(size_t)t * 2 * F + 2 * f] = (float)(w * c);
-    tw[(size_t)t * 2 * F + 2 * f + 1] = (float)(-w * s);
+    // angles reduced exactly in integers to 2 pi q with q = r / K in [-1/2, 1/2]
+    // (r, K < 2^24 are exact in FP32; the quotient is rounded once), then FP32
+    // sine and cosine of pi * 2q
+    long long r = (b * t) % K;
+    if (2 * r > K) r -= K;
+    const long long tt = 2 * t > K ? t - K : t;
+    float s, c;
+    sincospif(2.0f * __fdiv_rn((float)r, (float)K), &s, &c);
+    const float w = __fmul_rn(0.5f, __fsub_rn(1.0f, cospif(2.0f * __fdiv_rn((float)tt, (float)K))));
+    tw[(size_t)t * 2 * F + 2 * f] = __fmul_rn(w, c);
+    tw[(size_t)t * 2 * F + 2 * f + 1] = -__fmul_rn(w, s);
 }
 
 constexpr int TR = 64, TC = 64, TKC = 32;

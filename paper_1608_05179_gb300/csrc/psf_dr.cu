@@ -7,8 +7,9 @@
 // A'_ns = A_ns / (sqrt(d_n) sqrt(d_s)), which leaves the clamped iteration of
 // Eq. (14) unchanged step for step (x = x' / sqrt(d)).
 //
-// dr_diag_kernel: one warp per point, d_n in FP64 from the FP32 vectors, out as
-// sqrt(d_n).  dr_correct_kernel: the pair correction is a real Gram product of
+// dr_diag_kernel: one warp per point, d_n from the FP32 vectors as compensated
+// FP32 sums (TwoProduct terms, TwoSum accumulation, pairs through the warp
+// reduction; d_n is about 1 - 1/M, far from cancellation), out as sqrt(d_n).  dr_correct_kernel: the pair correction is a real Gram product of
 // the squared magnitudes, 64 x 64 output tiles on CUDA cores (K = microphones
 // staged through shared memory), fused with the rescaling and written in place;
 // every entry is read and written by one thread, and the FMA order is the same
@@ -17,28 +18,54 @@
 
 namespace {
 
+// (h, l) += a * b, error-free up to the final rounding of l
+__device__ __forceinline__ void acc_prod(float &h, float &l, float a, float b) {
+    float p, pe, t;
+    two_prod(a, b, p, pe);
+    two_sum(h, p, h, t);
+    l = __fadd_rn(l, __fadd_rn(t, pe));
+}
+
+// (h, l) summed over the warp, returned as h + l on every lane
+__device__ __forceinline__ float warp_pair_sum(float h, float l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        float t;
+        two_sum(h, h2, h, t);
+        l = __fadd_rn(__fadd_rn(l, l2), t);
+    }
+    return __fadd_rn(h, l);
+}
+
 __global__ void __launch_bounds__(256) dr_diag_kernel(const float *__restrict__ Lre, const float *__restrict__ Lim,
                                                       const float *__restrict__ Rre, const float *__restrict__ Rim,
-                                                      int ldm, int M, int S, double scale,
+                                                      int ldm, int M, int S, float scale,
                                                       float *__restrict__ dscale) {
     const int lane = threadIdx.x & 31;
     const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= S) return;
-    double gr = 0.0, gi = 0.0, t = 0.0;
+    float grh = 0.f, grl = 0.f, gih = 0.f, gil = 0.f, th = 0.f, tl = 0.f;
     for (int m = lane; m < M; m += 32) {
         const size_t o = (size_t)n * ldm + m;
-        const double lr = Lre[o], li = Lim[o], rr = Rre[o], ri = Rim[o];
-        gr += lr * rr + li * ri;  // conj(l) * r
-        gi += lr * ri - li * rr;
-        t += (lr * lr + li * li) * (rr * rr + ri * ri);
+        const float lr = Lre[o], li = Lim[o], rr = Rre[o], ri = Rim[o];
+        acc_prod(grh, grl, lr, rr);  // Re conj(l) r = lr rr + li ri
+        acc_prod(grh, grl, li, ri);
+        acc_prod(gih, gil, lr, ri);  // Im conj(l) r = lr ri - li rr
+        acc_prod(gih, gil, -li, rr);
+        acc_prod(th, tl, __fmaf_rn(lr, lr, __fmul_rn(li, li)), __fmaf_rn(rr, rr, __fmul_rn(ri, ri)));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gr += __shfl_xor_sync(0xffffffffu, gr, o);
-        gi += __shfl_xor_sync(0xffffffffu, gi, o);
-        t += __shfl_xor_sync(0xffffffffu, t, o);
+    const float gr = warp_pair_sum(grh, grl), gi = warp_pair_sum(gih, gil), t = warp_pair_sum(th, tl);
+    if (lane == 0) {
+        // |G|^2 - t with the squares error-free and one compensated sum
+        float p1, e1, p2, e2, s1, e3, s2, e4;
+        two_prod(gr, gr, p1, e1);
+        two_prod(gi, gi, p2, e2);
+        two_sum(p1, p2, s1, e3);
+        two_sum(s1, -t, s2, e4);
+        const float d = __fadd_rn(s2, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, e4)));
+        dscale[n] = __fsqrt_rn(fmaxf(__fmul_rn(scale, d), 0.f));
     }
-    if (lane == 0) dscale[n] = (float)sqrt(fmax(scale * (gr * gr + gi * gi - t), 0.0));
 }
 
 constexpr int TM = 64, TN = 64, TK = 16;
@@ -114,7 +141,7 @@ cudaError_t launch_psf_dr(const float *Lre, const float *Lim, const float *Rre, 
                           int S, float scale, float *A, int lda, float *dscale, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     dr_diag_kernel<<<(unsigned)(((size_t)S * 32 + 255) / 256), 256, 0, st>>>(Lre, Lim, Rre, Rim, ldm, M, S,
-                                                                             (double)scale, dscale);
+                                                                             scale, dscale);
     const dim3 grid((S + TN - 1) / TN, (S + TM - 1) / TM);
     dr_correct_kernel<<<grid, 256, 0, st>>>(Lre, Lim, Rre, Rim, ldm, M, S, scale, dscale, A, lda);
     return cudaGetLastError();

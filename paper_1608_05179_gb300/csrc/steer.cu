@@ -6,18 +6,35 @@
 // for x^-1/2, y' = y (3/2 - d^2 y^2 / 2), which takes the seed's relative error
 // e (a few 1e-7) to about 1.5 e^2 (below 2e-13), and d = d^2 y'.  The phase is
 // reduced to the fraction of a period t = d*f/c - rint(d*f/c) before an FP32
-// sin/cos of 2*pi*t, so the FP32 part only sees an argument in [-pi, pi].  The
-// amplitude |r|/d = |r| y' and ||g||^2 are formed in FP64 without a division.
+// sin/cos of 2*pi*t, so the FP32 part only sees an argument in [-pi, pi].
+// FP64 serves the distance and the phase only: the amplitude |r|/d = |r| y' is
+// an FP32 product of |r| and y' (rounded once), and ||g||^2 = sum_m (|r|/d_m)^2
+// is a compensated FP32 sum (TwoProduct per term, TwoSum accumulation, the
+// pairs carried through the warp reduction), accurate to about one FP32 ulp.
 // Time convention exp(+j w t): a wave travelling distance d picks up
 // exp(-j k d).
 #include "common.cuh"
 
 namespace {
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// (h, l) += a * a, error-free up to the final rounding of l
+__device__ __forceinline__ void acc_square(float &h, float &l, float a) {
+    float p, pe, t;
+    two_prod(a, a, p, pe);
+    two_sum(h, p, h, t);
+    l = __fadd_rn(l, __fadd_rn(t, pe));
+}
+
+// warp-wide sum of (h, l) pairs; every lane returns h + l
+__device__ __forceinline__ float warp_sum_pair(float h, float l) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        float t;
+        two_sum(h, h2, h, t);
+        l = __fadd_rn(__fadd_rn(l, l2), t);
+    }
+    return __fadd_rn(h, l);
 }
 
 // Microphone m seen from point (px, py, pz): cos and sin of the phase
@@ -47,22 +64,23 @@ __global__ void __launch_bounds__(256) steer_kernel(GeomK g, int kind, const int
     const int n = idx ? idx[warp] : warp;
     const int ix = n % g.nx, iy = n / g.nx;
     const double px = g.x0 + ix * g.dx, py = g.y0 + iy * g.dy, pz = g.z;
-    const double rabs = sqrt(px * px + py * py + pz * pz);
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    const float rabs = __fsqrt_rn(__fmaf_rn(pxf, pxf, __fmaf_rn(pyf, pyf, __fmul_rn(pzf, pzf))));
 
     // ||g||^2 = sum_m (|r| / d_m)^2; the terms of the first MAX_CACHED
     // microphones of this lane stay in registers for the output pass
     // (q = |r| / d, and d as FP32)
     float cc[MAX_CACHED], ss[MAX_CACHED], qq[MAX_CACHED], dd[MAX_CACHED];
-    double g2 = 0.0;
+    float g2h = 0.f, g2l = 0.f;
 #pragma unroll
     for (int j = 0; j < MAX_CACHED; ++j) {
         const int m = lane + 32 * j;
         if (m < g.M) {
             double d, inv_d;
             mic_term(g, m, px, py, pz, cc[j], ss[j], d, inv_d);
-            const double a = rabs * inv_d;
-            g2 = fma(a, a, g2);
-            qq[j] = (float)a;
+            const float a = __fmul_rn(rabs, (float)inv_d);
+            acc_square(g2h, g2l, a);
+            qq[j] = a;
             dd[j] = (float)d;
         }
     }
@@ -70,13 +88,11 @@ __global__ void __launch_bounds__(256) steer_kernel(GeomK g, int kind, const int
         float c, s;
         double d, inv_d;
         mic_term(g, m, px, py, pz, c, s, d, inv_d);
-        const double a = rabs * inv_d;
-        g2 = fma(a, a, g2);
+        acc_square(g2h, g2l, __fmul_rn(rabs, (float)inv_d));
     }
-    g2 = warp_sum_d(g2);
-    const double inv_norm = 1.0 / sqrt(g2);
-    const float inv_norm_f = (float)inv_norm, inv_rabs = (float)(1.0 / rabs);
-    if (gnorm2 && lane == 0) gnorm2[warp] = (float)g2;
+    const float g2 = warp_sum_pair(g2h, g2l);
+    const float inv_norm_f = __frsqrt_rn(g2), inv_rabs = __frcp_rn(rabs);
+    if (gnorm2 && lane == 0) gnorm2[warp] = g2;
 
     const size_t row = (size_t)warp * ldm;
     // q = |r| / d, dfl = d
@@ -104,7 +120,7 @@ __global__ void __launch_bounds__(256) steer_kernel(GeomK g, int kind, const int
         float c, s;
         double d, inv_d;
         mic_term(g, m, px, py, pz, c, s, d, inv_d);
-        put(m, c, s, (float)(rabs * inv_d), (float)d);
+        put(m, c, s, __fmul_rn(rabs, (float)inv_d), (float)d);
     }
     // zero padding of the plane rows
     for (int m = g.M + lane; m < ldm; m += 32) {

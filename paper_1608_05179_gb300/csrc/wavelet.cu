@@ -225,28 +225,42 @@ __global__ void gather_kernel(const float *__restrict__ src, const int32_t *__re
 constexpr int ST = 1024;
 
 // x_full = 0 everywhere, then x_full[idx[i]] = x_sub[i] / gnorm2[i]; total power
-// summed in FP64 in a fixed order (per-thread strided sums, fixed tree).
+// as a compensated FP32 sum (TwoSum per term, (hi, lo) pairs through a fixed
+// tree), in a fixed order; the pair is returned as the double hi + lo, which
+// holds it exactly (two FP32 significands fit in one FP64 significand).
 __global__ void __launch_bounds__(ST) scatter_power_kernel(const float *__restrict__ x_sub,
                                                            const int32_t *__restrict__ idx,
                                                            const float *__restrict__ gnorm2, int n,
                                                            float *__restrict__ x_full, int S,
                                                            double *__restrict__ total) {
-    __shared__ double red[ST];
+    __shared__ float red_h[ST], red_l[ST];
     for (int i = threadIdx.x; i < S; i += ST) x_full[i] = 0.0f;
     __syncthreads();
-    double acc = 0.0;
+    float h = 0.f, l = 0.f;
     for (int i = threadIdx.x; i < n; i += ST) {
         const float v = gnorm2 ? __fdiv_rn(x_sub[i], gnorm2[i]) : x_sub[i];
         x_full[idx ? idx[i] : i] = v;
-        acc += (double)v;
+        float t;
+        two_sum(h, v, h, t);
+        l = __fadd_rn(l, t);
     }
-    red[threadIdx.x] = acc;
+    red_h[threadIdx.x] = h;
+    red_l[threadIdx.x] = l;
     __syncthreads();
     for (int s = ST / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        if (threadIdx.x < s) {
+            float hh, t;
+            two_sum(red_h[threadIdx.x], red_h[threadIdx.x + s], hh, t);
+            red_h[threadIdx.x] = hh;
+            red_l[threadIdx.x] = __fadd_rn(__fadd_rn(red_l[threadIdx.x], red_l[threadIdx.x + s]), t);
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && total) *total = red[0];
+    if (threadIdx.x == 0 && total) {
+        float hh, t;
+        two_sum(red_h[0], red_l[0], hh, t);  // normalise: |t| <= ulp(hh) / 2
+        *total = (double)hh + (double)t;
+    }
 }
 
 }  // namespace
