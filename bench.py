@@ -296,7 +296,10 @@ def run_gpu(args, rank, world, local_rank):
     f_ms, f_sweep_ms, _ = timed(full_step, k_full, min(args.warmup, 3), C_dev)
     clock_info = clocks.stop()
     S_sub = int(c_res[0])
-    batched = batched_leg(ctx, D, dev, BATCH_BINS) if world == 1 else None
+    extra = world == 1 and args.legs == "all"
+    batched = batched_leg(ctx, D, dev, BATCH_BINS) if extra else None
+    band = band_figures(ctx, D, 3, autotune=False) if extra else None
+    serve = serve_figures(ctx, D, 16) if extra else None
 
     # e2e: CSM in from pinned host memory, power map out to pinned host memory, every step
     C_host = C_dev.cpu().pin_memory()
@@ -345,6 +348,8 @@ def run_gpu(args, rank, world, local_rank):
     ach_f = bytes_f / (sweep_f_ms / 1e3) / 1e9
     traffic = _traffic_from_profiles()
     latency = _handover_floor(D, ctx, S_sub, S, sweep_c_ms, sweep_f_ms)
+    chain = _chain_floors(D, ctx, sc, geom, C_dev, S_sub, sweep_c_ms, sweep_f_ms, latency["handover_ns_median"],
+                          hbm_peak)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -361,15 +366,20 @@ def run_gpu(args, rank, world, local_rank):
                      "traffic": traffic.get("sweep_spiral81_compressed"), "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_c, "launch_ms": round(sweep_c_ms, 4),
                      "note": "A (S~ x S~ FP32, 1.7 MB) is read once per sweep in the algorithm; the kernel reads "
-                             "it from L2 (tiles by TMA, fold entries by asynchronous copies) and from DRAM about "
-                             "once per launch, so the launch is bound by the sequential row chain, not HBM"},
+                             "only the columns of nonzero dx, from L2 (tiles by TMA, fold entries as vector loads) "
+                             "and from DRAM about once per launch, so the launch is bound by the sequential row "
+                             "chain, not HBM: see latency and bytes_needed",
+                     "latency": chain["compressed"]["latency"], "bytes_needed": chain["compressed"]["bytes_needed"]},
         "roofline_full_grid": {"kernel": "damas_sweep_kernel (full grid)", "bound": "hbm", "achieved": round(ach_f, 1),
                                "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_f / hbm_peak, 4),
                                "traffic": traffic.get("sweep_spiral81_full"), "algorithmic_bytes_per_launch": bytes_f,
-                               "launch_ms": round(sweep_f_ms, 3)},
+                               "launch_ms": round(sweep_f_ms, 3), "latency": chain["full_grid"]["latency"],
+                               "bytes_needed": chain["full_grid"]["bytes_needed"]},
         "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "latency_floor": latency,
         "batched": batched,
+        "band": band,
+        "serve": serve,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clock_info,
         "wall_s_compressed_region": round(wall, 3),
@@ -400,6 +410,54 @@ def _handover_floor(D, ctx, S_sub, S, sweep_c_ms, sweep_f_ms):
                               "form": "single CTA: no hand-overs; each 32-row step is the row chain and one "
                                       "CTA barrier"})
 
+    return out
+
+
+def _chain_floors(D, ctx, sc, geom, C_dev, S_sub, sweep_c_ms, sweep_f_ms, handover_ns, hbm_peak):
+    """Latency roofline of the sweeps.  One more solve of each benchmark system
+    (outside the timed region) counts its blocks, the rows that entered a block's
+    chain and the nonzero dx; damas_chain_probe measures, on this GPU, one
+    candidate update of the chain and one 512-thread barrier step.  The chain
+    floor is candidates x t_candidate + blocks x t_barrier (+ hand-overs x the
+    median one-way hand-over for a team): the time the sequential dependence of
+    Gauss-Seidel alone takes.  bytes_needed: the columns of A that the folds must
+    read (nonzero dx x S~ entries) plus the TMA tiles (four 32 x 32 boxes per
+    block step of the single-CTA form)."""
+    import torch
+    t_cand, t_bar = D.damas_chain_probe(ctx, 200000)
+    out = {}
+    b = D.das_map(ctx, geom, sc.freq, C_dev)
+    for name, compressed, ms in (("compressed", True, sweep_c_ms), ("full_grid", False, sweep_f_ms)):
+        if compressed:
+            idx, n_t, _, _ = D.wavelet_compress_grid(ctx, b, sc.grid.nx, sc.grid.ny, LEVELS, D.PRED_HAAR,
+                                                     D.EPS_KEEP_FRAC, KEEP)
+            n = int(n_t.item())
+            idx = idx[:n]
+            b_sub = D.damas_gather(ctx, b, idx, n)
+        else:
+            n, idx, b_sub = sc.grid.S, None, b
+        A, _ = D.damas_build_psf(ctx, geom, sc.freq, idx, n)
+        x = torch.zeros(n, dtype=torch.float32, device=b.device)
+        st = torch.zeros(3, dtype=torch.int64, device=b.device)
+        D.damas_solve(ctx, D.System(A, b_sub, x, ITERS), stats=st)
+        blocks, cand, nnz = (int(v) for v in st.cpu().tolist())
+        ncta, _, _ = D.damas_solve_plan(ctx, n, D.F32)
+        hand = ncta * ITERS if ncta > 1 else 0
+        floor_ms = (cand * t_cand + blocks * t_bar + hand * handover_ns) / 1e6
+        tiles = blocks * 4 * 32 * 32 * 4 if ncta == 1 else 0
+        need = float(nnz) * n * 4 + tiles
+        out[name] = {
+            "latency": {"bound": "latency", "achieved_row_steps_per_s": round(float(n) * ITERS / (ms / 1e3), 1),
+                        "blocks": blocks, "candidate_rows": cand, "nonzero_dx": nnz, "handovers": hand,
+                        "t_candidate_ns": round(t_cand, 2), "t_barrier_ns": round(t_bar, 2),
+                        "floor_ms": round(floor_ms, 3), "launch_ms": round(ms, 3), "frac": round(floor_ms / ms, 4),
+                        "what": "candidates x t_candidate + blocks x t_barrier + hand-overs x median hand-over "
+                                "(damas_chain_probe, damas_handover_probe, solve statistics), against the launch"},
+            "bytes_needed": {"bytes": need, "gbs": round(need / (ms / 1e3) / 1e9, 2),
+                             "frac_of_hbm": round(need / (ms / 1e3) / 1e9 / hbm_peak, 5),
+                             "what": "nonzero dx x S~ x 4 B (the columns of A the folds read) + TMA tiles; "
+                                     "mostly served from L2"}}
+        del A
     return out
 
 
@@ -502,10 +560,22 @@ def run_band(args):
     """64 bins log-spaced 1-8 kHz on a 121x121 grid, each bin compressed (linear
     prediction, 3 levels, relative threshold 1e-3), 1000 sweeps, all bins in one
     solve launch replayed from a CUDA graph; FP32 and BF16 storage of A."""
-    import torch
-    from paper_1608_05179_gb300 import band as BD
     from paper_1608_05179_gb300 import damas as D
     ctx = D.Context(0)
+    out = band_figures(ctx, D, args.steps, args.rows, autotune=not args.rows)
+    ctx.close()
+    return out
+
+
+# the autotuner's choice for this band on GB300 (band.autotune_rows): 512 rows per CTA, two CTAs per SM
+BAND_PLAN_ROWS = 512
+
+
+def band_figures(ctx, D, reps: int, rows: int = 0, autotune: bool = True):
+    """The band workload's figures (see run_band); rows > 0 fixes the team plan
+    (rows per CTA, two CTAs per SM) instead of running the autotuner."""
+    import torch
+    from paper_1608_05179_gb300 import band as BD
     scenes = synth.scene_band_121(n_bins=64)
     geom = D.Geometry.from_scene(scenes[0].mics, scenes[0].grid, scenes[0].c)
     freqs = [s.freq for s in scenes]
@@ -515,9 +585,10 @@ def run_band(args):
     out = {"metric": "band bins/s (64 bins, one solve launch)", "unit": "freq-bins/s", "workload":
            "band: 64 bins 1-8 kHz, 121x121 grid, M=64 spiral, 5 sources, linear L=3 rel 1e-3, 1000 sweeps",
            "S_f_min": min(grids.S_f), "S_f_max": max(grids.S_f), "S_f_sum": sum(grids.S_f)}
+    sms = torch.cuda.get_device_properties(geom.mic_xyz.device).multi_processor_count
     for name, dt, elt in (("f32", D.F32, 4), ("bf16", D.BF16, 2)):
-        if args.rows:
-            plan, tune = ("rows", args.rows, None), None
+        if not autotune:
+            plan, tune = ("rows", rows or BAND_PLAN_ROWS, 2 * sms), None
         else:
             plan, tune = BD.autotune_rows(ctx, geom, freqs, grids, iters_probe=20, a_dtype=dt)
         bs = BD.plan_solver(ctx, geom, freqs, grids.S_f, 1000, dt, plan)
@@ -527,11 +598,11 @@ def run_band(args):
         bs.check()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(reps):
             bs.replay()
         e1.record()
         bs.check()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / reps
         replayed = [x.clone() for x in bs.x]
         # the solve launch alone (it also re-checks the replayed results, bit for bit)
         systems = bs.systems()
@@ -550,7 +621,8 @@ def run_band(args):
                      "largest_bin_ctas": bs.ctas[int(np.argmax(grids.S_f))],
                      "autotune_s_per_20_sweeps": {f"{k[0]} {k[1]} x{k[2]}": round(v, 4) for k, v in tune.items()}
                      if tune else None}
-    ctx.close()
+        del bs
+        torch.cuda.empty_cache()
     return out
 
 
@@ -653,6 +725,18 @@ def _serve_stream(D, SV, ctx, specs, full: bool):
             "bins": bins, "rows_solved": rows, "bins_per_s": round(bins / span, 2), "span_s": round(span, 2)}
 
 
+def serve_figures(ctx, D, n_requests: int):
+    """A short Poisson stream of the serving workload (200 req/s; M, grid side,
+    bins, kept fraction and sources drawn per request), served on the compressed
+    grids and then, the same requests, on the full grids: p50/p99 latency and
+    bins/s of each."""
+    from paper_1608_05179_gb300 import serve as SV
+    specs = synth.serve_requests(seed=5, n=n_requests)
+    return {"workload": f"{len(specs)} requests, Poisson 200 req/s, 1000 sweeps per bin",
+            "compressed": _serve_stream(D, SV, ctx, specs, full=False),
+            "full_grid": _serve_stream(D, SV, ctx, specs, full=True)}
+
+
 def run_serve(args):
     """Poisson stream (200 req/s) of independent requests: M in {32,64,128}, grid side
     in {41,81,121,161}, 1-32 bins in 1-10 kHz, kept fraction 2-30%, 1-6 sources,
@@ -742,6 +826,8 @@ def main():
     ap.add_argument("--rows", type=int, default=0, help="band: rows per CTA (0 = chosen by the autotuner)")
     ap.add_argument("--requests", type=int, default=32, help="serve: number of requests")
     ap.add_argument("--serve-full", action="store_true", help="serve: also serve the stream on the full grids")
+    ap.add_argument("--legs", default="all", choices=["all", "core"],
+                    help="spiral81: 'core' runs only the compressed and full-grid legs (for profiling runs)")
     args = ap.parse_args()
     if args.workload != "spiral81":
         from paper_1608_05179_gb300 import build as B

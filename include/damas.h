@@ -358,6 +358,11 @@ typedef struct {
     int withhold_block;   /* test hook for the bounded waits, 0 in normal use: when > 0 the
                              owner of row block (withhold_block - 1) never publishes it, so
                              the waits of the other CTAs for it run out */
+    uint64_t *stats_dev;  /* optional device uint64[3], added to by the call: 32-row blocks
+                             solved, rows that entered a block's chain (those that could
+                             move; systems of one block leave this out), nonzero dx
+                             entries.  For measurement: the sequential chain's length and
+                             the columns of A the folds must read */
 } damas_solve_cfg;
 
 /*
@@ -451,6 +456,20 @@ int damas_solve_plan(damas_ctx *ctx, int S, int lda, int a_dtype, int ctas, int 
  */
 int damas_handover_probe(damas_ctx *ctx, int rounds, int max_pairs, int timeout_us, double *ns_host, int *n_pairs,
                          damas_stream stream);
+
+/*
+ * Measurement aid, not part of the method: the latency of the row chain of a
+ * block solve on this device.  One CTA of 512 threads: warp 0 runs `rounds`
+ * dependent candidate updates as a block solve does them (broadcast of the
+ * candidate's w by shuffle, the clamp as a max with -x, one FMA into every
+ * lane's w), then all 16 warps run `rounds` CTA-barrier steps.
+ *   rounds   1..10000000.
+ *   ns_host  host double[2] output: ns per candidate update, ns per barrier step.
+ * Synchronises the stream.  With the counts of damas_solve_cfg.stats_dev,
+ * candidates x ns[0] + blocks x ns[1] is the time the sweep's sequential
+ * dependence alone takes on one CTA.
+ */
+int damas_chain_probe(damas_ctx *ctx, int rounds, double *ns_host, damas_stream stream);
 
 /* ------------------------------------------------------------------ serving */
 

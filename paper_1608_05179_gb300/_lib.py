@@ -38,7 +38,7 @@ class damas_system(ctypes.Structure):
 
 class damas_solve_cfg(ctypes.Structure):
     _fields_ = [("ctas_per_system", c_int), ("timeout_ms", c_int), ("status_dev", c_void_p),
-                ("a_placement", c_int), ("withhold_block", c_int)]
+                ("a_placement", c_int), ("withhold_block", c_int), ("stats_dev", c_void_p)]
 
 
 class damas_mixed_system(ctypes.Structure):
@@ -98,6 +98,7 @@ SIGNATURES = {
                                  ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "damas_handover_probe": (c_int, [c_void_p, c_int, c_int, c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(c_int), c_void_p]),
+    "damas_chain_probe": (c_int, [c_void_p, c_int, ctypes.POINTER(ctypes.c_double), c_void_p]),
     "damas_serve_start": (c_int, [c_void_p, ctypes.POINTER(damas_serve_cfg)]),
     "damas_serve_submit": (c_int, [c_void_p, ctypes.POINTER(damas_request), ctypes.POINTER(ctypes.c_uint64)]),
     "damas_serve_poll": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(damas_result)]),

@@ -97,6 +97,9 @@ cudaError_t launch_csm(const float *p, int M, long long T, int K, int hop, const
 size_t handover_probe_bytes(int npairs);
 cudaError_t launch_handover_probe(void *work, int rounds, int npairs, unsigned long long timeout_ns, cudaStream_t st,
                                   double **out_ns, int **status);
+// Row-chain latency probe: out_dev[0] ns per candidate update of a block
+// solve, out_dev[1] ns per barrier step of a 512-thread CTA; sink_dev: 33 floats.
+cudaError_t launch_chain_probe(int rounds, double *out_dev, float *sink_dev, cudaStream_t st);
 // Neighbour padding of a grid-index set (one CTA): marks (bytes, S of them)
 // is scratch.
 cudaError_t launch_pad_grid(int nx, int ny, const int32_t *idx, const int32_t *n_in, int radius, int32_t *out,

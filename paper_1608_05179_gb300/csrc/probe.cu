@@ -72,7 +72,49 @@ __global__ void __launch_bounds__(32) handover_probe_kernel(unsigned long long *
     }
 }
 
+// Latency of the Gauss-Seidel sweep's row chain (a measurement aid): warp 0
+// runs `rounds` dependent candidate updates exactly as a block solve does them
+// (the candidate's w broadcast by shuffle, the clamp as a max with -x, one FMA
+// into every lane's w), then the whole CTA of SOLO_THREADS threads runs
+// `rounds` barrier steps.  out[0]: ns per candidate update, out[1]: ns per
+// barrier step.
+constexpr int CHAIN_PROBE_THREADS = 512;
+__global__ void __launch_bounds__(CHAIN_PROBE_THREADS, 1) chain_probe_kernel(int rounds, double *out, float *sink) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ unsigned long long t_start;
+    float w = 1e-3f * (float)(lane + 1), xneg = -0.5f * (float)lane;
+    const float a = 0.25f + 1e-3f * (float)lane;
+    if (warp == 0) {
+        __syncwarp();
+        const unsigned long long t0 = now_ns();
+        for (int i = 0; i < rounds; ++i) {
+            const int j = (i * 7) & 31;
+            const float wj = __shfl_sync(0xffffffffu, w, j);
+            const float d = fmaxf(wj, __shfl_sync(0xffffffffu, xneg, j));
+            w = __fmaf_rn(-a, d, w);
+        }
+        __syncwarp();
+        if (lane == 0) out[0] = (double)(now_ns() - t0) / rounds;
+        sink[lane] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) t_start = now_ns();
+    __syncthreads();
+    int acc = 0;
+    for (int i = 0; i < rounds; ++i) {
+        acc += (i ^ warp) & 1;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[1] = (double)(now_ns() - t_start) / rounds;
+    if (acc < 0) sink[32] = (float)acc;
+}
+
 }  // namespace
+
+cudaError_t launch_chain_probe(int rounds, double *out_dev, float *sink_dev, cudaStream_t st) {
+    chain_probe_kernel<<<1, CHAIN_PROBE_THREADS, 0, st>>>(rounds, out_dev, sink_dev);
+    return cudaGetLastError();
+}
 
 size_t handover_probe_bytes(int npairs) { return (size_t)(npairs + 1) * 128 + (size_t)npairs * sizeof(double) + 128; }
 

@@ -140,12 +140,14 @@ __device__ __forceinline__ void prefetch_tiles(const SweepSys &s, const Team &T,
     cp_async_commit();
 }
 
-// The nonzero entries of a 32-wide dx vector as a compact list (warp 0).
-__device__ __forceinline__ void make_list(float d, unsigned char *idx, int *cnt) {
+// The nonzero entries of a 32-wide dx vector as a compact list (warp 0);
+// returns their number.
+__device__ __forceinline__ int make_list(float d, unsigned char *idx, int *cnt) {
     const int lane = threadIdx.x & 31;
     const unsigned m = __ballot_sync(FULL, d != 0.f);
     if (d != 0.f) idx[__popc(m & ((1u << lane) - 1u))] = (unsigned char)lane;
     if (lane == 0) *cnt = __popc(m);
+    return __popc(m);
 }
 
 // Compensated sum over the listed columns c of A[row0 + r][c0 + c] * d[c], in
@@ -384,7 +386,7 @@ __device__ __forceinline__ void block_bound(const SweepSys &s, const Team &T, co
 template <bool F32, bool RES>
 __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As, const char *tiles, int J, int Jm1,
                                               float *xs, const float *rh, const float *rl, const float *bnd,
-                                              float dprev, bool have_prev, bool nonneg) {
+                                              float dprev, bool have_prev, bool nonneg, int &ncand) {
     const int k = threadIdx.x & 31;
     const int i = J * 32 + k, r = i - T.row0;
     const bool valid = i < T.S;
@@ -452,6 +454,7 @@ __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As,
         mask = __ballot_sync(FULL, valid);
     }
 
+    ncand = __popc(mask);
     const float xneg = -x_old;
     float dchain = 0.f;
     if (__popc(mask) > 16) {
@@ -496,7 +499,7 @@ __device__ __forceinline__ float solve_block2(const Team &T, const uint32_t *As,
     return __fsub_rn(x_new, x_old);
 }
 
-template <bool F32, bool RES>
+template <bool F32, bool RES, bool STATS>
 __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &s, float (*dring)[32],
                                           unsigned char (*nzidx)[32], int *nzcnt, int *s_abort_p, char *smem) {
     int &s_abort = *s_abort_p;
@@ -516,6 +519,8 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
     const long long Gend = (long long)s.iters * nb;
     const int elt = F32 ? 4 : 2;
     bool nonneg_all = true;
+    // warp 0: blocks solved, rows that entered the chain, nonzero dx (launch statistics)
+    unsigned long long st_solves = 0, st_cand = 0, st_nnz = 0;
 
     float *rh = (float *)smem;
     float *rl = rh + T.R;
@@ -628,7 +633,11 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
             if (warp == 0) {
                 const float dk = solve_block<F32, RES>(T, As, tiles, 0, 0, xs, rh, rl, nullptr, nonneg_all);
                 dring[gi][lane] = dk;
-                make_list(dk, nzidx[gi], &nzcnt[gi]);
+                const int nzk = make_list(dk, nzidx[gi], &nzcnt[gi]);
+                if (STATS) {
+                    st_nnz += nzk;
+                    ++st_solves;
+                }
             }
             __syncthreads();
             if (warp != 0 && warp != 4 && nzcnt[gi]) {
@@ -654,14 +663,20 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
                         __syncwarp();
                     }
                 }
+                int nc;
                 const float dk =
-                    solve_block2<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, bnd, dprev, true, nonneg_all);
+                    solve_block2<F32, RES>(T, As, tl, J, Jm1, xs, rh, rl, bnd, dprev, true, nonneg_all, nc);
                 dprev = dk;
+                if (STATS) st_cand += nc;
                 if (J != p.withhold_block)
                     st_relaxed_u64(s.mbox + (size_t)J * 32 + lane,
                                    ((unsigned long long)epoch << 32) | __float_as_uint(dk));
                 dring[gi][lane] = dk;
-                make_list(dk, nzidx[gi], &nzcnt[gi]);
+                const int nzk = make_list(dk, nzidx[gi], &nzcnt[gi]);
+                if (STATS) {
+                    st_nnz += nzk;
+                    ++st_solves;
+                }
                 if (!RES && ring) {
                     // the slot just used takes the own block TSLOTS - 1 solves ahead
                     __syncwarp();
@@ -777,6 +792,11 @@ __device__ __forceinline__ void sweep_cta(const SweepParams &p, const SweepSys &
         const long long G = Gend - 2 + (threadIdx.x >> 5);
         s.state[2 * S + threadIdx.x] = pipelined ? dring[G & 3][lane] : 0.f;
     }
+    if (STATS && threadIdx.x == 0) {
+        atomicAdd(p.stats, st_solves);
+        atomicAdd(p.stats + 1, st_cand);
+        atomicAdd(p.stats + 2, st_nnz);
+    }
     if (warp == 0 && !RES) cp_async_wait_all();
 }
 
@@ -794,6 +814,7 @@ __device__ __forceinline__ bool upstream_failed(const SweepParams &p) {
 
 // At most 128 registers a thread, so that two CTAs of streamed teams fit on an SM
 // (a batch of teams then runs side by side in one launch).
+template <bool STATS>
 __global__ void __launch_bounds__(SW_THREADS, 2) damas_sweep_kernel(const SweepParams p) {
     extern __shared__ __align__(16) char smem[];
     __shared__ float dring[4][32];
@@ -807,14 +828,14 @@ __global__ void __launch_bounds__(SW_THREADS, 2) damas_sweep_kernel(const SweepP
     // one specialised body per storage type and placement, chosen once per CTA
     if (s.dtype == DAMAS_F32) {
         if (s.resident)
-            sweep_cta<true, true>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+            sweep_cta<true, true, STATS>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
         else
-            sweep_cta<true, false>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+            sweep_cta<true, false, STATS>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
     } else {
         if (s.resident)
-            sweep_cta<false, true>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+            sweep_cta<false, true, STATS>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
         else
-            sweep_cta<false, false>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
+            sweep_cta<false, false, STATS>(p, s, dring, nzidx, nzcnt, &s_abort, smem);
     }
 }
 
@@ -1048,7 +1069,7 @@ __device__ __forceinline__ void solo_fold(const SweepSys &s, const Team &T, int 
     }
 }
 
-template <bool F32>
+template <bool F32, bool STATS>
 __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys &s, const CUtensorMap *map,
                                            float (*dring)[32], unsigned char (*nzidx)[32], int *nzcnt,
                                            unsigned long long *tbar, int *s_abort_p, char *smem) {
@@ -1069,6 +1090,8 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
     const int elt = F32 ? 4 : 2;
     const bool upd = solo_updater(warp);
     const int ut = upd ? solo_upd_index(warp) * 32 + lane : 0;
+    // warp 0: blocks solved, rows that entered the chain, nonzero dx (launch statistics)
+    unsigned long long st_solves = 0, st_cand = 0, st_nnz = 0;
 
     // tile slots first, 128-byte aligned for TMA; then the rows
     char *tiles = smem + ((128u - (smem_addr(smem) & 127u)) & 127u);
@@ -1168,11 +1191,17 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
         const int gi = (int)(G & 3), g1 = (gi + 3) & 3, g2 = (gi + 2) & 3;
         const char *slot = tiles + sl * slot_bytes;
         if (warp == 0) {
+            int nc;
             const float dk = solve_block2<F32, false>(T, nullptr, slot, J, Jm1, xs, rh, rl, bnd, dprev, true,
-                                                      nonneg_all);
+                                                      nonneg_all, nc);
             dprev = dk;
             dring[gi][lane] = dk;
-            make_list(dk, nzidx[gi], &nzcnt[gi]);
+            const int nzk = make_list(dk, nzidx[gi], &nzcnt[gi]);
+            if (STATS) {
+                st_nnz += nzk;
+                st_cand += nc;
+                ++st_solves;
+            }
         } else if (warp == 1) {
             // block J+1: dx_{G-2} (which a call resumed from a state already folded
             // there), then dx_{G-1}
@@ -1241,8 +1270,14 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
         const long long Gx = Gend - 2 + (threadIdx.x >> 5);
         s.state[2 * S + threadIdx.x] = dring[Gx & 3][lane];
     }
+    if (STATS && threadIdx.x == 0) {
+        atomicAdd(p.stats, st_solves);
+        atomicAdd(p.stats + 1, st_cand);
+        atomicAdd(p.stats + 2, st_nnz);
+    }
 }
 
+template <bool STATS>
 __global__ void __launch_bounds__(SOLO_THREADS, 1)
     damas_sweep_solo_kernel(const SweepParams p, const __grid_constant__ SoloMaps maps) {
     extern __shared__ __align__(16) char smem[];
@@ -1254,9 +1289,9 @@ __global__ void __launch_bounds__(SOLO_THREADS, 1)
     if (upstream_failed(p)) return;
     const SweepSys s = p.sys[blockIdx.x];
     if (s.dtype == DAMAS_F32)
-        sweep_solo<true>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
+        sweep_solo<true, STATS>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
     else
-        sweep_solo<false>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
+        sweep_solo<false, STATS>(p, s, &maps.m[blockIdx.x], dring, nzidx, nzcnt, tbar, &s_abort, smem);
 }
 
 }  // namespace
@@ -1271,14 +1306,22 @@ size_t sweep_smem_bytes(int R, int lda, int dtype, bool resident) {
     return b;
 }
 
+// The two instantiations (with and without launch statistics) have the same
+// resources (at most 128 registers a thread): the occupancy of the plain one
+// serves both.
 cudaError_t sweep_occupancy(size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(damas_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(damas_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, damas_sweep_kernel, SW_THREADS, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, damas_sweep_kernel<false>, SW_THREADS, smem);
 }
 
-cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(damas_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+
+template <bool STATS>
+cudaError_t launch_sweep_t(const SweepParams &p, int grid, size_t smem, cudaStream_t st) {
+    auto kern = damas_sweep_kernel<STATS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // Teams only wait on their own members.  When every team has the same size
     // (2..16 CTAs) the launch is one thread-block cluster per team: a cluster is
@@ -1289,7 +1332,7 @@ cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream
     bool same = p.nsys >= 1 && p.sys[0].ncta >= 2 && p.sys[0].ncta <= 16;
     for (int i = 1; same && i < p.nsys; ++i) same = p.sys[i].ncta == p.sys[0].ncta;
     if (same && grid == p.nsys * p.sys[0].ncta &&
-        cudaFuncSetAttribute(damas_sweep_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
         cudaLaunchConfig_t cc = {};
         cc.gridDim = dim3(grid);
         cc.blockDim = dim3(SW_THREADS);
@@ -1303,8 +1346,8 @@ cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream
         cc.attrs = ca;
         cc.numAttrs = 1;
         int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, damas_sweep_kernel, &cc) == cudaSuccess && ncl >= p.nsys)
-            return cudaLaunchKernelEx(&cc, damas_sweep_kernel, p);
+        if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cc) == cudaSuccess && ncl >= p.nsys)
+            return cudaLaunchKernelEx(&cc, kern, p);
         cudaGetLastError();  // a refused cluster query leaves no error behind
     }
     cudaLaunchConfig_t cfg = {};
@@ -1317,7 +1360,24 @@ cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, damas_sweep_kernel, p);
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <bool STATS>
+cudaError_t launch_sweep_solo_t(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(damas_sweep_solo_kernel<STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // no CTA waits on another: a plain launch, one CTA per system
+    damas_sweep_solo_kernel<STATS><<<p.nsys, SOLO_THREADS, smem, st>>>(p, maps);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// The statistics instantiation only when the caller asks for the counts.
+cudaError_t launch_sweep(const SweepParams &p, int grid, size_t smem, cudaStream_t st) {
+    return p.stats ? launch_sweep_t<true>(p, grid, smem, st) : launch_sweep_t<false>(p, grid, smem, st);
 }
 
 size_t sweep_solo_smem_bytes(int R, int dtype) {
@@ -1354,17 +1414,13 @@ bool make_sweep_tile_map(CUtensorMap *m, const void *At, int dtype, int lda, int
 }
 
 cudaError_t sweep_solo_occupancy(size_t smem, int *blocks_per_sm) {
-    cudaError_t e =
-        cudaFuncSetAttribute(damas_sweep_solo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(damas_sweep_solo_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, damas_sweep_solo_kernel, SOLO_THREADS, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, damas_sweep_solo_kernel<false>, SOLO_THREADS,
+                                                         smem);
 }
 
 cudaError_t launch_sweep_solo(const SweepParams &p, const SoloMaps &maps, size_t smem, cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(damas_sweep_solo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    // no CTA waits on another: a plain launch, one CTA per system
-    damas_sweep_solo_kernel<<<p.nsys, SOLO_THREADS, smem, st>>>(p, maps);
-    return cudaGetLastError();
+    return p.stats ? launch_sweep_solo_t<true>(p, maps, smem, st) : launch_sweep_solo_t<false>(p, maps, smem, st);
 }

@@ -24,6 +24,7 @@ struct SweepParams {
     int *status;
     unsigned long long timeout_ns;
     int withhold_block;  // test hook: block index never published, or -1
+    unsigned long long *stats;  // optional [3]: blocks solved, rows that entered the chain, nonzero dx (added to)
     const int *upstream; // the context's build status word, or nullptr: when it holds an error at
                          // launch (a build kernel gave up a wait, so A may hold NaN), the launch
                          // reports DAMAS_ETIMEDOUT and leaves x unchanged

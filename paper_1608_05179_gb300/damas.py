@@ -285,16 +285,19 @@ PLACE_AUTO, PLACE_RESIDENT, PLACE_STREAM = 0, 1, 2
 
 def damas_solve(ctx: Context, systems, ctas_per_system: int = 0, timeout_ms: int = 0,
                 status: torch.Tensor | None = None, a_placement: int = PLACE_AUTO, withhold_block: int = 0,
-                stream=None):
+                stats: torch.Tensor | None = None, stream=None):
     """DAMAS Gauss-Seidel sweeps (Eq. (13)-(14)) on a batch of systems in one persistent launch:
     one CTA per system (small systems, when every system of the call qualifies) or a team
-    of CTAs per system; both forms give bit-identical x and state."""
+    of CTAs per system; both forms give bit-identical x and state.  stats (optional int64
+    device tensor of 3) is added to: blocks solved, rows that entered a chain, nonzero dx."""
     if isinstance(systems, System):
         systems = [systems]
     arr = (_lib.damas_system * len(systems))(*[s.cstruct() for s in systems])
+    if stats is not None and (stats.dtype != torch.int64 or stats.numel() < 3):
+        raise ValueError("stats must be an int64 tensor of 3")
     cfg = _lib.damas_solve_cfg(int(ctas_per_system), int(timeout_ms),
                                status.data_ptr() if status is not None else None, int(a_placement),
-                               int(withhold_block))
+                               int(withhold_block), stats.data_ptr() if stats is not None else None)
     ctx.check(ctx.lib.damas_solve(ctx.handle, arr, len(systems), ctypes.byref(cfg), _stream(stream)))
     return systems
 
@@ -321,6 +324,13 @@ def damas_handover_probe(ctx: Context, rounds: int = 100, max_pairs: int = 1 << 
     return [buf[i] for i in range(n.value)]
 
 
+def damas_chain_probe(ctx: Context, rounds: int = 100000, stream=None):
+    """Row-chain latency on this device: (ns per candidate update, ns per 512-thread barrier step)."""
+    out = (ctypes.c_double * 2)()
+    ctx.check(ctx.lib.damas_chain_probe(ctx.handle, int(rounds), out, _stream(stream)))
+    return out[0], out[1]
+
+
 def solve_mixed(ctx: Context, A_bf16: torch.Tensor, A_f32: torch.Tensor, b: torch.Tensor, x: torch.Tensor,
                 iters_bulk: int, iters_refine: int, At_bf16: torch.Tensor | None = None,
                 At_f32: torch.Tensor | None = None, ctas: int = 0, ctas_per_system: int = 0, timeout_ms: int = 0,
@@ -336,7 +346,7 @@ def solve_mixed(ctx: Context, A_bf16: torch.Tensor, A_f32: torch.Tensor, b: torc
                                 int(A_f32.shape[1]), S, b.data_ptr(), x.data_ptr(), int(iters_bulk),
                                 int(iters_refine), int(ctas))
     cfg = _lib.damas_solve_cfg(int(ctas_per_system), int(timeout_ms),
-                               status.data_ptr() if status is not None else None, int(a_placement), 0)
+                               status.data_ptr() if status is not None else None, int(a_placement), 0, None)
     ctx.check(ctx.lib.damas_solve_mixed(ctx.handle, ctypes.byref(m), 1, ctypes.byref(cfg), _stream(stream)))
     return x
 

@@ -238,3 +238,31 @@ def test_solo_and_team_systems_in_one_call(ctx):
     D.damas_solve(ctx, batch)
     for s, x in zip(batch, alone):
         assert torch.equal(s.x, x)
+
+
+def test_solve_statistics_agree_between_forms(ctx):
+    """The launch statistics (blocks solved, rows that entered a chain, nonzero
+    dx) count the iteration itself, so the single-CTA form and a team report the
+    same numbers; blocks solved = sweeps x blocks."""
+    A64, b64 = compressed_system()
+    S, iters = len(b64), 200
+    nb = -(-S // 32)
+    out = []
+    for ctas, place in ((1, 2), (5, 2), (0, 1)):
+        A = padded(A64)
+        b = torch.as_tensor(b64.astype(np.float32), device="cuda")
+        x = torch.zeros(S, device="cuda")
+        st = torch.zeros(3, dtype=torch.int64, device="cuda")
+        D.damas_solve(ctx, D.System(A, b, x, iters), ctas_per_system=ctas, a_placement=place, stats=st)
+        out.append(st.cpu().numpy().tolist())
+    print("[stats]", out)
+    assert out[0] == out[1] == out[2]
+    solves, cand, nnz = out[0]
+    assert solves == iters * nb
+    assert 0 < nnz <= cand <= solves * 32
+
+
+def test_chain_probe(ctx):
+    t_cand, t_bar = D.damas_chain_probe(ctx, 20000)
+    print(f"[chain probe] {t_cand:.1f} ns per candidate, {t_bar:.1f} ns per barrier step")
+    assert 1.0 < t_cand < 1000.0 and 1.0 < t_bar < 5000.0
