@@ -159,6 +159,17 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
                     int S_sub, int a_dtype, void *A_dev, int lda, float *gnorm2_dev, damas_stream stream);
 
 /*
+ * The same PSF matrix in both storage types at once, for the mixed-precision
+ * schedule (damas_solve_mixed): one FP32 build as damas_build_psf, then its BF16
+ * copy rounded to nearest even, which is bit for bit what damas_build_psf with
+ * DAMAS_BF16 stores.  A_f32_dev: device float S_sub x lda; A_bf16_dev: device
+ * bfloat16 S_sub x lda (not overlapping it); other arguments as damas_build_psf.
+ */
+int damas_build_psf_f32_bf16(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev,
+                             int S_sub, float *A_f32_dev, void *A_bf16_dev, int lda, float *gnorm2_dev,
+                             damas_stream stream);
+
+/*
  * PSF with the CSM diagonal removed (§2), for geom->diag_removal = 1 (which
  * damas_build_psf rejects): the response at point n to a unit source at s
  * without the m = m' microphone pairs,

@@ -77,6 +77,8 @@ SIGNATURES = {
     "damas_state_floats": (c_int, [c_int]),
     "damas_build_psf": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_int, c_void_p,
                                 c_int, c_void_p, c_void_p]),
+    "damas_build_psf_f32_bf16": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_void_p,
+                                         c_void_p, c_int, c_void_p, c_void_p]),
     "das_map": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_void_p, c_void_p]),
     "damas_build_psf_dr": (c_int, [c_void_p, ctypes.POINTER(damas_geom), c_double, c_void_p, c_int, c_void_p, c_int,
                                    c_void_p, c_void_p, c_void_p]),

@@ -214,6 +214,19 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     return DAMAS_OK;
 }
 
+int damas_build_psf_f32_bf16(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev,
+                             int S_sub, float *A_f32_dev, void *A_bf16_dev, int lda, float *gnorm2_dev,
+                             damas_stream stream) {
+    if (!ctx) return DAMAS_EINVAL;
+    if (!A_bf16_dev) return ctx_fail(ctx, DAMAS_EINVAL, "A_bf16_dev is NULL");
+    if ((void *)A_f32_dev == A_bf16_dev) return ctx_fail(ctx, DAMAS_EINVAL, "the two outputs must not overlap");
+    int rc = damas_build_psf(ctx, geom, freq_hz, idx_dev, S_sub, DAMAS_F32, A_f32_dev, lda, gnorm2_dev, stream);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    DAMAS_CUDA_TRY(ctx, launch_to_bf16(A_f32_dev, A_bf16_dev, (size_t)S_sub * lda, (cudaStream_t)stream));
+    return DAMAS_OK;
+}
+
 int damas_build_psf_dr(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev, int S_sub,
                        float *A_dev, int lda, float *gnorm2_dev, float *dscale_dev, damas_stream stream) {
     if (!ctx) return DAMAS_EINVAL;

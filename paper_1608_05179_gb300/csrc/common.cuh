@@ -80,6 +80,8 @@ cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre
                             int M, int S, float scale, void *A, int lda, int a_dtype, float *work, int *status,
                             unsigned long long timeout_ns, int hold, cudaStream_t st);
 size_t psf_work_floats(int S, int ldm, bool symmetric);
+// dst[i] = bfloat16(src[i]) (round to nearest even), i < n.
+cudaError_t launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st);
 // b_n = scale * Re(L_n^H C L_n) for n < S (dr: without the terms of C's diagonal).
 cudaError_t launch_das(const float *Lre, const float *Lim, int ldm, int M, int S, const float *C, float scale,
                        float *b, int dr, cudaStream_t st);

@@ -512,6 +512,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// BF16 copy of an FP32 matrix (round to nearest even, as the BF16 Gram epilogue
+// stores), four entries a thread when both pointers allow vector access.
+__global__ void __launch_bounds__(256) to_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
+                                                      size_t n, int vec) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        if (4 * t + 3 < n) {
+            const float4 v = reinterpret_cast<const float4 *>(src)[t];
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+            uint2 w;
+            w.x = *reinterpret_cast<const uint32_t *>(&lo);
+            w.y = *reinterpret_cast<const uint32_t *>(&hi);
+            reinterpret_cast<uint2 *>(dst)[t] = w;
+        }
+    } else if (t < n) {
+        dst[t] = __float2bfloat16_rn(src[t]);
+    }
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -615,5 +634,13 @@ cudaError_t launch_psf_gram(const float *Lre, const float *Lim, const float *Rre
                                                                symmetric ? 1 : 0, ntx, (int)ntiles, timeout_ns,
                                                                status, hold);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float *src, void *dst, size_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int vec = n % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 && reinterpret_cast<uintptr_t>(dst) % 8 == 0;
+    const size_t work = vec ? n / 4 : n;
+    to_bf16_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(src, (__nv_bfloat16 *)dst, n, vec);
     return cudaGetLastError();
 }

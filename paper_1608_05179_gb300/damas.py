@@ -143,6 +143,26 @@ def damas_build_psf(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor
     return A, gnorm2
 
 
+def damas_build_psf_f32_bf16(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor | None = None,
+                             S_sub: int | None = None, A: torch.Tensor | None = None,
+                             A_bf16: torch.Tensor | None = None, gnorm2: torch.Tensor | None = None, stream=None):
+    """The PSF matrix in FP32 and in BF16 from one build; returns (A, A_bf16, gnorm2)."""
+    S_sub = geom.S if idx is None and S_sub is None else (S_sub if S_sub is not None else int(idx.numel()))
+    lda = damas_lda(S_sub)
+    dev = geom.mic_xyz.device
+    if A is None:
+        A = torch.empty((S_sub, lda), dtype=torch.float32, device=dev)
+    if A_bf16 is None:
+        A_bf16 = torch.empty((S_sub, lda), dtype=torch.bfloat16, device=dev)
+    if gnorm2 is None:
+        gnorm2 = torch.empty(S_sub, dtype=torch.float32, device=dev)
+    g = geom.cstruct()
+    ctx.check(ctx.lib.damas_build_psf_f32_bf16(ctx.handle, ctypes.byref(g), float(freq), _ptr(idx), int(S_sub),
+                                               _ptr(A), _ptr(A_bf16), int(A.shape[1]), _ptr(gnorm2),
+                                               _stream(stream)))
+    return A, A_bf16, gnorm2
+
+
 def damas_build_psf_dr(ctx: Context, geom: Geometry, freq: float, idx: torch.Tensor | None = None,
                        S_sub: int | None = None, A: torch.Tensor | None = None, gnorm2: torch.Tensor | None = None,
                        dscale: torch.Tensor | None = None, stream=None):

@@ -103,3 +103,17 @@ def test_solve_mixed_in_one_call_equals_the_two_solves(ctx, nb, nr):
     x2 = torch.zeros_like(x)
     D.solve_mixed(ctx, Abf, A32, b, x2, nb, nr)
     assert torch.equal(x2, refs[0])
+
+
+def test_psf_in_both_storage_types_equals_the_two_builds(ctx):
+    """damas_build_psf_f32_bf16: the FP32 matrix of damas_build_psf(F32) and the BF16
+    matrix of damas_build_psf(BF16), bit for bit, from one build (ragged size)."""
+    sc = synth.scene_spiral_81()
+    geom = D.Geometry.from_scene(sc.mics, sc.grid, sc.c)
+    idx = torch.as_tensor(np.arange(5, 6561, 9, dtype=np.int32), device="cuda")    # 729 points
+    A32, g2 = D.damas_build_psf(ctx, geom, sc.freq, idx, int(idx.numel()))
+    Abf, _ = D.damas_build_psf(ctx, geom, sc.freq, idx, int(idx.numel()), a_dtype=D.BF16)
+    B32, Bbf, h2 = D.damas_build_psf_f32_bf16(ctx, geom, sc.freq, idx)
+    torch.cuda.synchronize()
+    assert torch.equal(A32, B32) and torch.equal(g2, h2)
+    assert torch.equal(Abf.view(torch.int16), Bbf.view(torch.int16))
