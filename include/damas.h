@@ -142,7 +142,8 @@ int damas_state_floats(int S);
  * points (Eq. (24)) when idx_dev is given.
  *   idx_dev   device int32[S_sub], ascending grid indices, or NULL for all
  *             S = nx*ny points in order (then S_sub must equal S).
- *   A_dev     device, S_sub x lda, row-major, lda = damas_lda(S_sub); FP32 when
+ *   A_dev     device, S_sub x lda, row-major, lda = damas_lda(S_sub), 16-byte
+ *             aligned (the solver reads its rows by TMA and 16-byte vectors); FP32 when
  *             a_dtype = DAMAS_F32, bfloat16 when DAMAS_BF16.  A[n][m] for the
  *             n-th and m-th selected points; the diagonal is stored as exactly 1;
  *             padding columns S_sub..lda-1 are written as 0.
@@ -163,7 +164,8 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
  * schedule (damas_solve_mixed): one FP32 build as damas_build_psf, then its BF16
  * copy rounded to nearest even, which is bit for bit what damas_build_psf with
  * DAMAS_BF16 stores.  A_f32_dev: device float S_sub x lda; A_bf16_dev: device
- * bfloat16 S_sub x lda (not overlapping it); other arguments as damas_build_psf.
+ * bfloat16 S_sub x lda, 16-byte aligned, not overlapping A_f32_dev (DAMAS_EINVAL
+ * otherwise); other arguments as damas_build_psf.
  */
 int damas_build_psf_f32_bf16(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const int32_t *idx_dev,
                              int S_sub, float *A_f32_dev, void *A_bf16_dev, int lda, float *gnorm2_dev,
@@ -195,7 +197,7 @@ int damas_divide(damas_ctx *ctx, float *v_dev, const float *div_dev, int n, dama
 /*
  * Mean-square DAS map of Eq. (2) on the full grid.
  *   C_dev  device, M x M complex cross-spectral matrix (Eq. (1)), row-major,
- *          interleaved (re, im) FP32 pairs; assumed Hermitian.
+ *          interleaved (re, im) FP32 pairs, 8-byte aligned; assumed Hermitian.
  *   b_dev  device float[nx*ny] output, FP32, real part of v^H C v (scaled as
  *          the formulation says); with geom->diag_removal the terms of the CSM
  *          diagonal are left out.
@@ -216,7 +218,8 @@ int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float 
  * vector a, the form das_map takes (the same exp(-j k d) convention).
  *   p_dev     device float[M][T] (row-major; T >= K).
  *   bins_dev  device int32[F]: DFT bin indices, 0..K/2 (bin f is bins[f] * fs / K Hz).
- *   C_dev     device float[F][M][M][2] output, interleaved (re, im), exactly Hermitian.
+ *   C_dev     device float[F][M][M][2] output, interleaved (re, im), 8-byte aligned,
+ *             exactly Hermitian.
  * Limits: M 1..DAMAS_MAX_MICS, K 2..1048576, hop >= 1, F 1..4096, M * L <= 4194240.
  * The DFT of the selected bins runs as a tiled product of the sample blocks
  * with a window-and-twiddle table (angles reduced exactly in integers to a
@@ -338,14 +341,15 @@ enum {
 };
 
 typedef struct {
-    const void *A_dev;  /* S x lda, row-major, FP32 or BF16 (a_dtype), unit diagonal;
+    const void *A_dev;  /* S x lda, row-major, FP32 or BF16 (a_dtype), unit diagonal,
+                           16-byte aligned (as At_dev; b, x and state float-aligned);
                            entries >= 0 (PSF matrices are) let rows that cannot move be
                            skipped exactly; a block with a negative entry is solved in full */
     const void *At_dev; /* A transposed, same type and lda, or NULL when A is symmetric
                            (formulation E).  Read when A's rows are not held in shared
                            memory: column c of A is then read as row c of At */
     int a_dtype;        /* DAMAS_F32 or DAMAS_BF16 */
-    int lda;            /* row stride in elements, multiple of 8, >= S */
+    int lda;            /* row stride in elements, multiple of 32, >= S (damas_lda) */
     int S;              /* number of unknowns, >= 1 */
     const float *b_dev; /* device float[S] */
     float *x_dev;       /* device float[S], in/out */

@@ -43,6 +43,9 @@ int ctx_ensure(damas_ctx *ctx, ScratchBuf &b, size_t bytes) {
 
 namespace {
 
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -189,6 +192,8 @@ int damas_build_psf(damas_ctx *ctx, const damas_geom *geom, double freq_hz, cons
     if (!idx_dev && S_sub != S) return ctx_fail(ctx, DAMAS_EINVAL, "S_sub must equal nx*ny when idx is NULL");
     if (a_dtype != DAMAS_F32 && a_dtype != DAMAS_BF16) return ctx_fail(ctx, DAMAS_EINVAL, "bad a_dtype");
     if (!A_dev) return ctx_fail(ctx, DAMAS_EINVAL, "A_dev is NULL");
+    if (!aligned(A_dev, 16)) return ctx_fail(ctx, DAMAS_EINVAL, "A_dev must be 16-byte aligned");
+    if (gnorm2_dev && !aligned(gnorm2_dev, 4)) return ctx_fail(ctx, DAMAS_EINVAL, "gnorm2_dev must be float-aligned");
     if (lda < S_sub || lda % 32) return ctx_fail(ctx, DAMAS_EINVAL, "lda=%d must be a multiple of 32 and >= S_sub", lda);
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -219,7 +224,12 @@ int damas_build_psf_f32_bf16(damas_ctx *ctx, const damas_geom *geom, double freq
                              damas_stream stream) {
     if (!ctx) return DAMAS_EINVAL;
     if (!A_bf16_dev) return ctx_fail(ctx, DAMAS_EINVAL, "A_bf16_dev is NULL");
-    if ((void *)A_f32_dev == A_bf16_dev) return ctx_fail(ctx, DAMAS_EINVAL, "the two outputs must not overlap");
+    if (!aligned(A_bf16_dev, 16)) return ctx_fail(ctx, DAMAS_EINVAL, "A_bf16_dev must be 16-byte aligned");
+    if (A_f32_dev && S_sub > 0 && lda > 0) {
+        const uintptr_t f0 = (uintptr_t)A_f32_dev, f1 = f0 + (uintptr_t)S_sub * lda * 4;
+        const uintptr_t b0 = (uintptr_t)A_bf16_dev, b1 = b0 + (uintptr_t)S_sub * lda * 2;
+        if (f0 < b1 && b0 < f1) return ctx_fail(ctx, DAMAS_EINVAL, "the two outputs must not overlap");
+    }
     int rc = damas_build_psf(ctx, geom, freq_hz, idx_dev, S_sub, DAMAS_F32, A_f32_dev, lda, gnorm2_dev, stream);
     if (rc) return rc;
     DeviceGuard dg(ctx->device);
@@ -282,6 +292,8 @@ int damas_csm(damas_ctx *ctx, const float *p_dev, int M, long long T, int K, int
     if (T < K) return ctx_fail(ctx, DAMAS_EINVAL, "T=%lld shorter than one block", T);
     if (F < 1 || F > 4096) return ctx_fail(ctx, DAMAS_EINVAL, "F=%d out of range", F);
     if (!p_dev || !bins_dev || !C_dev) return ctx_fail(ctx, DAMAS_EINVAL, "NULL pointer");
+    if (!aligned(C_dev, 8) || !aligned(p_dev, 4) || !aligned(bins_dev, 4))
+        return ctx_fail(ctx, DAMAS_EINVAL, "C_dev must be 8-byte aligned (complex), p_dev and bins_dev 4-byte");
     const long long L = (T - K) / hop + 1;
     if ((long long)M * L > 65535ll * 64) return ctx_fail(ctx, DAMAS_EINVAL, "M*L=%lld too large", (long long)M * L);
     DeviceGuard dg(ctx->device);
@@ -300,6 +312,8 @@ int das_map(damas_ctx *ctx, const damas_geom *geom, double freq_hz, const float 
     if (rc) return rc;
     if (!(freq_hz > 0.0)) return ctx_fail(ctx, DAMAS_EINVAL, "frequency must be positive");
     if (!C_dev || !b_dev) return ctx_fail(ctx, DAMAS_EINVAL, "C_dev and b_dev are required");
+    if (!aligned(C_dev, 8) || !aligned(b_dev, 4))
+        return ctx_fail(ctx, DAMAS_EINVAL, "C_dev must be 8-byte aligned (complex), b_dev 4-byte");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int S = geom->nx * geom->ny;
@@ -379,6 +393,8 @@ int damas_scatter_power(damas_ctx *ctx, const float *x_sub_dev, const int32_t *i
     if (S < 1 || n < 0 || n > S || !x_full_dev || (n > 0 && !x_sub_dev))
         return ctx_fail(ctx, DAMAS_EINVAL, "bad scatter arguments");
     if (!idx_dev && n != S) return ctx_fail(ctx, DAMAS_EINVAL, "n must equal S when idx is NULL");
+    if (total_power_dev && !aligned(total_power_dev, 8))
+        return ctx_fail(ctx, DAMAS_EINVAL, "total_power_dev must be 8-byte aligned");
     DeviceGuard dg(ctx->device);
     DAMAS_CUDA_TRY(ctx, launch_scatter_power(x_sub_dev, idx_dev, gnorm2_dev, n, x_full_dev, S, total_power_dev,
                                              (cudaStream_t)stream));
@@ -625,6 +641,11 @@ int check_systems(damas_ctx *ctx, const damas_system *sys, int nsys) {
         const damas_system &s = sys[i];
         if (s.S < 1) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: S=%d", i, s.S);
         if (!s.A_dev || !s.b_dev || !s.x_dev) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: NULL pointer", i);
+        // rows of A are read as 16-byte vectors and by TMA, whose base must be 16-byte aligned
+        if (!aligned(s.A_dev, 16) || (s.At_dev && !aligned(s.At_dev, 16)))
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: A_dev and At_dev must be 16-byte aligned", i);
+        if (!aligned(s.b_dev, 4) || !aligned(s.x_dev, 4) || (s.state_dev && !aligned(s.state_dev, 4)))
+            return ctx_fail(ctx, DAMAS_EINVAL, "system %d: b_dev, x_dev and state_dev must be float-aligned", i);
         if (s.a_dtype != DAMAS_F32 && s.a_dtype != DAMAS_BF16) return ctx_fail(ctx, DAMAS_EINVAL, "system %d: a_dtype", i);
         if (s.lda < round_up(s.S, 32) || s.lda % 32)
             return ctx_fail(ctx, DAMAS_EINVAL, "system %d: lda=%d must be a multiple of 32 and >= S rounded up to 32", i,
