@@ -887,7 +887,7 @@ __device__ __forceinline__ void solo_tma_box(uint32_t dst, const CUtensorMap *ma
         : "memory");
 }
 
-// Helper warp, one thread: the four tiles of step G (block J) into one slot,
+// The TMA thread (warp 4, lane 0): the four tiles of step G (block J) into one slot,
 // tile(Y, X)[j][k] = At[32X + j][32Y + k]: (J, J) the chain, (J, J-1) warp 0's
 // partial, (J+1, J-2) and (J+1, J-1) the helper's fold into block J+1.
 __device__ __forceinline__ void solo_issue_tiles(const CUtensorMap *map, const Team &T, char *slot, uint32_t bar,
@@ -1101,7 +1101,7 @@ __device__ __forceinline__ void sweep_solo(const SweepParams &p, const SweepSys 
         }
     }
     __syncthreads();
-    // tile slots of steps 0 .. SOLO_PD-1 (helper thread); phase bit q: parity of
+    // tile slots of steps 0 .. SOLO_PD-1 (the TMA thread); phase bit q: parity of
     // the next completion of slot q
     uint32_t phase = 0;
     if (warp == 4 && lane == 0)
