@@ -109,7 +109,13 @@ enum {
      * Gram launch on the context first wait for a device flag that nothing sets,
      * so the wait runs out after the build timeout and the launch takes its abort
      * path (no GPU fault is involved).  Set it back to 0 to build normally. */
-    DAMAS_OPT_TEST_HOLD_BUILD = 2
+    DAMAS_OPT_TEST_HOLD_BUILD = 2,
+    /* Cap, in bytes, on the device memory the context holds (0, the default: no
+     * cap).  Scratch that would take the context above it is refused with
+     * DAMAS_ENOMEM (nothing is freed or launched); it is also the serving loop's
+     * request budget when damas_serve_cfg.hbm_budget_bytes is 0.  A cap below
+     * what the context already holds is refused with DAMAS_EINVAL. */
+    DAMAS_OPT_HBM_BUDGET_BYTES = 3
 };
 int damas_set_option(damas_ctx *ctx, int option, long long value);
 
@@ -507,7 +513,8 @@ int damas_chain_probe(damas_ctx *ctx, int rounds, double *ns_host, damas_stream 
  * granted when no other request is solving, so a small budget slows the loop
  * but never stalls it (the budget can then be exceeded by that one request). */
 typedef struct {
-    size_t hbm_budget_bytes; /* device memory the loop may hold for requests; 0 = half the free memory */
+    size_t hbm_budget_bytes; /* device memory the loop may hold for requests; 0 = the context's
+                                DAMAS_OPT_HBM_BUDGET_BYTES if set, else half the free memory */
     int max_inflight;        /* requests on the device at once; 0 = 32 */
     int sm_slots;            /* half-SM units that concurrent solves may hold together; 0 = twice the SM
                                 count (the whole device).  A solve is charged by the library's plan of

@@ -14,7 +14,7 @@ F32, BF16 = 1, 2
 PRED_LINEAR, PRED_HAAR = 0, 1
 EPS_ABS, EPS_REL_MAX, EPS_KEEP_FRAC = 0, 1, 2
 INIT_ZERO, INIT_X, INIT_STATE = 0, 1, 2
-OPT_BUILD_TIMEOUT_MS, OPT_TEST_HOLD_BUILD = 1, 2
+OPT_BUILD_TIMEOUT_MS, OPT_TEST_HOLD_BUILD, OPT_HBM_BUDGET_BYTES = 1, 2, 3
 
 ERROR_NAMES = {0: "DAMAS_OK", -1: "DAMAS_EINVAL", -2: "DAMAS_ENOMEM", -3: "DAMAS_ECUDA", -4: "DAMAS_ETIMEDOUT",
                -5: "DAMAS_EBUSY", -6: "DAMAS_ENOTFOUND"}

@@ -22,8 +22,21 @@ int ctx_fail(damas_ctx *ctx, int code, const char *fmt, ...) {
     return code;
 }
 
+// Device memory the context holds as scratch.
+size_t ctx_scratch_bytes(const damas_ctx *ctx) {
+    return ctx->planes.cap + ctx->wave.cap + ctx->solve.cap + ctx->status.cap + ctx->misc.cap + ctx->pad.cap +
+           ctx->probe.cap + ctx->kstat.cap;
+}
+
 int ctx_ensure(damas_ctx *ctx, ScratchBuf &b, size_t bytes) {
     if (bytes <= b.cap) return DAMAS_OK;
+    {
+        const size_t cap = (std::max(bytes, (size_t)1 << 20) + 4095) / 4096 * 4096;
+        const size_t others = ctx_scratch_bytes(ctx) - b.cap;
+        if (ctx->hbm_budget && others + cap > ctx->hbm_budget)
+            return ctx_fail(ctx, DAMAS_ENOMEM, "scratch of %zu bytes would take the context to %zu bytes, above its budget of %zu",
+                            cap, others + cap, ctx->hbm_budget);
+    }
     if (b.ptr) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return ctx_fail(ctx, DAMAS_ECUDA, "sync before scratch growth: %s", cudaGetErrorString(e));
@@ -150,6 +163,13 @@ int damas_set_option(damas_ctx *ctx, int option, long long value) {
         case DAMAS_OPT_BUILD_TIMEOUT_MS:
             if (value < 1 || value > 600000) return ctx_fail(ctx, DAMAS_EINVAL, "build timeout %lld ms", value);
             ctx->build_timeout_ms = (int)value;
+            return DAMAS_OK;
+        case DAMAS_OPT_HBM_BUDGET_BYTES:
+            if (value < 0) return ctx_fail(ctx, DAMAS_EINVAL, "HBM budget %lld bytes", value);
+            if (value > 0 && (size_t)value < ctx_scratch_bytes(ctx))
+                return ctx_fail(ctx, DAMAS_EINVAL, "HBM budget %lld bytes is below the %zu the context already holds",
+                                value, ctx_scratch_bytes(ctx));
+            ctx->hbm_budget = (size_t)value;
             return DAMAS_OK;
         case DAMAS_OPT_TEST_HOLD_BUILD:
             if (value != 0 && value != 1) return ctx_fail(ctx, DAMAS_EINVAL, "test hold must be 0 or 1");

@@ -30,6 +30,7 @@ struct damas_ctx {
     ScratchBuf probe;    // hand-over probe words
     ScratchBuf kstat;    // build status word: DAMAS_ETIMEDOUT once a build kernel's wait ran out (sticky)
     int build_timeout_ms = 2000;  // bound on the build kernels' device waits
+    size_t hbm_budget = 0;        // cap on the context's device memory (scratch, serving default); 0 = none
     int test_hold = 0;            // test hook of those waits (damas_set_option)
     unsigned int epoch = 0;      // mailbox epoch of the solver exchange buffers
     struct ServeState *serve = nullptr;  // serving loop, when started

@@ -402,6 +402,7 @@ int damas_serve_start(damas_ctx *ctx, const damas_serve_cfg *cfg) {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
         st->cfg.hbm_budget_bytes = fr / 2;
+        if (ctx->hbm_budget) st->cfg.hbm_budget_bytes = ctx->hbm_budget;  // the context's own cap
     }
     st->device = ctx->device;
     st->sm_count = ctx->sm_count;

@@ -107,7 +107,8 @@ class Geometry:
 
 def damas_set_option(ctx: Context, option: int, value: int):
     """Context option: _lib.OPT_BUILD_TIMEOUT_MS (bound on the build kernels'
-    device waits) or _lib.OPT_TEST_HOLD_BUILD (test hook of those waits)."""
+    device waits), _lib.OPT_TEST_HOLD_BUILD (test hook of those waits) or
+    _lib.OPT_HBM_BUDGET_BYTES (cap on the context's device memory; 0 = none)."""
     ctx.check(ctx.lib.damas_set_option(ctx.handle, int(option), int(value)))
 
 

@@ -90,3 +90,39 @@ def test_dual_psf_rejects_overlap_and_misalignment(ctx, small):
     r16, _ = D.damas_build_psf(ctx, g, small.freq, a_dtype=D.BF16)
     torch.cuda.synchronize()
     assert torch.equal(A32, r32) and torch.equal(A16, r16)
+
+
+def test_context_hbm_budget_refuses_scratch_beyond_it(small):
+    """DAMAS_OPT_HBM_BUDGET_BYTES: scratch that would take the context above the
+    cap is refused with DAMAS_ENOMEM (the context stays usable); a cap below what
+    it holds, or a negative one, is refused with DAMAS_EINVAL; 0 lifts the cap."""
+    c = D.Context(0)
+    try:
+        sc = synth.scene_spiral_81()
+        g = D.Geometry.from_scene(sc.mics, sc.grid, sc.c)
+        with pytest.raises(D.DamasError):
+            D.damas_set_option(c, L.OPT_HBM_BUDGET_BYTES, -1)
+        D.damas_set_option(c, L.OPT_HBM_BUDGET_BYTES, 2 << 20)   # 2 MiB: below the 81x81 PSF's planes
+        A = torch.empty((g.S, D.damas_lda(g.S)), dtype=torch.float32, device="cuda")
+        g2 = torch.empty(g.S, dtype=torch.float32, device="cuda")
+        with pytest.raises(D.DamasError) as e:
+            D.damas_build_psf(c, g, sc.freq, A=A, gnorm2=g2)
+        assert e.value.code == L.DAMAS_ENOMEM
+        # the small grid's scratch fits the same cap
+        gs = D.Geometry.from_scene(small.mics, small.grid, small.c)
+        As, _ = D.damas_build_psf(c, gs, small.freq)
+        assert torch.isfinite(As).all()
+        with pytest.raises(D.DamasError):
+            D.damas_set_option(c, L.OPT_HBM_BUDGET_BYTES, (1 << 20) - 4096)   # below what the context holds now
+        D.damas_set_option(c, L.OPT_HBM_BUDGET_BYTES, 0)
+        D.damas_build_psf(c, g, sc.freq, A=A, gnorm2=g2)
+        torch.cuda.synchronize()
+        c2 = D.Context(0)
+        try:
+            ref, _ = D.damas_build_psf(c2, g, sc.freq)
+            torch.cuda.synchronize()
+        finally:
+            c2.close()
+        assert torch.equal(A, ref)
+    finally:
+        c.close()
