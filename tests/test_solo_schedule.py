@@ -84,3 +84,41 @@ def test_a_dropped_fold_is_caught():
                 recv[b].append(G - 2)
     complete = all(recv[b] == list(range(0, (Gend - 3 if b == nb - 1 else Gend - 2) + 1)) for b in range(nb))
     assert not complete
+
+
+# ---- which warps run the single-CTA steps (a mismatch between the named
+# barrier's thread count and the warps that reach it would stall the CTA)
+SOLO_THREADS, SOLO_UPD_THREADS = 512, 352
+
+
+def solo_updater(w):
+    return w >= 2 and (w & 3) != 0
+
+
+def solo_upd_index(w):
+    return w - 2 - (w >> 2)
+
+
+@pytest.mark.parametrize("S", [97, 127, 128, 129, 255, 256, 300, 657, 1023, 1024, 1280, 1281, 1408, 1409, 2000, 4096,
+                               8000])
+def test_step_barrier_counts_the_warps_that_reach_it(S):
+    n_upd_rows = min(SOLO_UPD_THREADS // 32, (S + 127) // 128)
+    n_active = 3 + n_upd_rows + (1 if n_upd_rows < SOLO_UPD_THREADS // 32 else 0)
+    nwarps = SOLO_THREADS // 32
+    active = [w == 0 or w == 1 or w == 4 or w == nwarps - 1 or (solo_updater(w) and solo_upd_index(w) < n_upd_rows)
+              for w in range(nwarps)]
+    assert sum(active) == n_active
+    # every group of four rows belongs to an updater thread of an active warp,
+    # and the warps left out hold no group (thread ut holds groups ut, ut + 352, ...)
+    groups = (S + 3) // 4
+    owner = {}
+    for w in range(nwarps):
+        if not solo_updater(w):
+            continue
+        for lane in range(32):
+            ut = solo_upd_index(w) * 32 + lane
+            for g in range(ut, groups, SOLO_UPD_THREADS):
+                assert g not in owner
+                owner[g] = w
+    assert sorted(owner) == list(range(groups))
+    assert all(active[w] for w in owner.values())
